@@ -1,0 +1,354 @@
+"""Benchmark of the Splotch per-frame rendering path on GB300.
+
+Workload (one "step" = one whole frame: transform, colorize, depth sort,
+tile binning, tile render): 10M particles in two species (gas in 1000
+Plummer spheres plus a uniform background, dark matter around the same
+centres), 1920x1080, absorptive, front to back over depth-sorted particles;
+seeded synthetic data resident in HBM.  Metric: particles rendered per
+second (all input particles / frame time), frames/s and p50/p99 frame
+latency.  Under torchrun every rank renders its own frame (replicas, weak
+scaling) and the slowest rank sets the time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "config1: 10M particles, gas 6M (1000 Plummer spheres + 20% uniform) and dark matter 4M, 1920x1080, absorptive"
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+RENDER_PROFILE = os.path.join(ROOT, "profiles", "k_render_config1_1080p_absorptive.txt")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the emission, e2e and CPU legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples taken while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        time.sleep(0.2)
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def render_profile_traffic():
+    """DRAM bytes per render launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    try:
+        txt = open(RENDER_PROFILE).read()
+    except OSError:
+        return None
+    src = open(os.path.join(ROOT, "paper_1004_1302_gb300", "csrc", "render.cu"), "rb").read()
+    digest = hashlib.sha256(src).hexdigest()[:16]
+    m = re.search(r"render_cu_sha256_16:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if m and t and m.group(1) == digest:
+        return float(t.group(1))
+    return None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(MEASURED))
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+def run_reference(args, world, rank):
+    """The oracle (FP64 CPU renderer) on the machine's host cores, each step a
+    bounded sample of the same workload."""
+    if rank != 0:
+        return
+    import synth
+    from oracle import oracle as O
+    O.build()
+    ps, cam = synth.config1()
+    step = 16
+    sub = ps.subsample(step)
+    pal = synth.colormap()
+    for _ in range(args.warmup):
+        O.render_frame(sub, cam, pal, O.ABSORPTIVE, tile=16)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.render_frame(sub, cam, pal, O.ABSORPTIVE, tile=16)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = sub.n / dt
+    cores = O.num_threads()
+    sample = f"every {step}th particle of each species ({sub.n} of {ps.n}), full 1920x1080 absorptive frame"
+    print(json.dumps({
+        "impl": "reference", "metric": "particles rendered/s (1920x1080, absorptive)", "value": value,
+        "unit": "particles/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": sub.n, "width": 1920, "height": 1080, "mode": "absorptive"},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(ps, cam, pal):
+    import synth  # noqa: F401
+    from oracle import oracle as O
+    O.build()
+    step = 8
+    sub = ps.subsample(step)
+    t0 = time.perf_counter()
+    O.render_frame(sub, cam, pal, O.ABSORPTIVE, tile=16)
+    dt = time.perf_counter() - t0
+    return {"value": sub.n / dt, "unit": "particles/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"every {step}th particle of each species ({sub.n} of {ps.n}), one full 1920x1080 "
+                      f"absorptive frame, {dt:.1f} s"}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_1004_1302_gb300 import splotch as S
+
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    if rank == 0:
+        S.build()
+    if world > 1:
+        dist.barrier()
+    S.load()
+
+    ps, cam = synth.config1()
+    pal = synth.colormap()
+    dp = S.upload(ps, dev, "f32")
+    fr = S.Frame(dp, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev)
+    fr.render()                      # sizes the tile-entry capacity for this workload
+    info = fr.info()
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        fr.run()
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    launches0 = S.splotch_launch_count()
+    with ClockSampler(dev.index if dev.index is not None else 0) as clocks:
+        barrier()
+        torch.cuda.synchronize(dev)
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for k in range(K):
+            e = ev[k]
+            e[0].record(stream)
+            fr.transform()
+            fr.colorize()
+            e[1].record(stream)
+            fr.sort()
+            e[2].record(stream)
+            fr.bin()
+            e[3].record(stream)
+            fr.render_tiles()
+            e[4].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    launches = S.splotch_launch_count() - launches0
+    total_ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    frame_ms = sorted(e[0].elapsed_time(e[4]) for e in ev)
+    stage = {
+        "transform_colorize": float(np.mean([e[0].elapsed_time(e[1]) for e in ev])),
+        "sort": float(np.mean([e[1].elapsed_time(e[2]) for e in ev])),
+        "bin": float(np.mean([e[2].elapsed_time(e[3]) for e in ev])),
+        "render": float(np.mean([e[3].elapsed_time(e[4]) for e in ev])),
+    }
+    ms_per_step = total_ms / K
+    value = world * ps.n * K / (total_ms * 1e-3)
+    final_status = fr.info().status
+    F = fr.fragments()
+    clk = clocks.summary()
+
+    out = {
+        "metric": "particles rendered/s (1920x1080, absorptive)", "value": value, "unit": "particles/s",
+        "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": ps.n, "visible": int(info.visible),
+                   "tile_entries": int(info.tile_entries), "fragments": F, "width": 1920, "height": 1080,
+                   "mode": "absorptive", "tile": args.tile, "batch": args.batch,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (200 MB particle arrays, >1 GB workspace per frame)"},
+        "frames_per_s": world * K / (total_ms * 1e-3),
+        "p50_ms": frame_ms[len(frame_ms) // 2],
+        "p99_ms": frame_ms[min(len(frame_ms) - 1, int(math.ceil(0.99 * len(frame_ms))) - 1)],
+        "stages_ms": stage,
+        "fragments_per_s": world * F * K / (total_ms * 1e-3),
+        "gpu_launches": int(launches),
+        "status": int(final_status),
+    }
+    mhz = clk["sm_mhz"] or 1425.0
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    # Render roofline: each fragment needs 14 FP32 operations and 2 exp2 in the
+    # absorptive integral of Eq. 1 (9 and 1 in emission); peaks from unit counts
+    # (128 FP32 lanes, 16 exp2 per SM per clock) at the sampled SM clock.
+    t_r = stage["render"] * 1e-3
+    fp32_peak = sms * 128 * mhz * 1e6
+    mufu_peak = sms * 16 * mhz * 1e6
+    fp32_frac = F * 14 / t_r / fp32_peak
+    mufu_frac = F * 2 / t_r / mufu_peak
+    traffic = render_profile_traffic()
+    out["roofline"] = {
+        "kernel": "k_render", "bound": "alu", "achieved": F * 14 / t_r / 1e12, "peak": fp32_peak / 1e12,
+        "unit": "TFLOP/s", "frac": max(fp32_frac, mufu_frac), "traffic": traffic,
+        "fp32_frac": fp32_frac, "mufu_frac": mufu_frac, "mufu_achieved_tex2_per_s": F * 2 / t_r / 1e12,
+        "mufu_peak_tex2_per_s": mufu_peak / 1e12, "sm_count": sms, "sm_mhz": mhz,
+        "algorithmic": "F fragments x (14 FP32 ops + 2 exp2) per launch; F counted on the device",
+    }
+    peaks = measured_peaks()
+    tc_bytes = ps.n * 20 + info.visible * 8
+    out["streaming"] = {
+        "transform_colorize_GBps": tc_bytes / (stage["transform_colorize"] * 1e-3) / 1e9,
+        "transform_colorize_frac_of_measured_hbm": tc_bytes / (stage["transform_colorize"] * 1e-3) / 1e9
+        / peaks["hbm_gbs"],
+        "sort_GBps": 4 * (info.visible * 20) / (stage["sort"] * 1e-3) / 1e9,
+        "hbm_peak_GBps": peaks["hbm_gbs"],
+    }
+    out["clocks"] = clk
+
+    if not args.quick:
+        # emission mode on the same particles
+        fe = S.Frame(dp, cam, pal, S.EMISSION, tile=args.tile, batch=args.batch, device=dev)
+        fe.render()
+        for _ in range(3):
+            fe.run()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(K):
+            fe.run()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ems = a.elapsed_time(b) / K
+        out["emission"] = {"value": ps.n / (ems * 1e-3), "unit": "particles/s", "ms_per_step": ems,
+                           "frames_per_s": 1e3 / ems}
+        del fe
+        # end to end through the public API with host buffers
+        host = [torch.from_numpy(a).pin_memory() for a in (ps.x, ps.y, ps.z, ps.h, ps.v)]
+        img_host = torch.empty((1080, 1920, 3), dtype=torch.float32).pin_memory()
+        dev_cols = [dp.x, dp.y, dp.z, dp.h, dp.v]
+        torch.cuda.synchronize(dev)
+        barrier()
+        a.record(stream)
+        for _ in range(K):
+            for d, h in zip(dev_cols, host):
+                d.copy_(h, non_blocking=True)
+            fr.run()
+            img_host.copy_(fr.image, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = a.elapsed_time(b) / K
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        out["e2e"] = {"value": world * ps.n / (e2e_ms * 1e-3), "unit": "particles/s",
+                      "h2d_bytes_per_step": int(sum(h.numel() * h.element_size() for h in host)),
+                      "d2h_bytes_per_step": int(img_host.numel() * 4), "ms_per_step": e2e_ms}
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(ps, cam, pal)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

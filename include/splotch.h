@@ -1,0 +1,242 @@
+/*
+ * splotch.h -- C ABI of the GB300 Splotch per-frame rendering path.
+ *
+ * The method is the particle renderer of Jin et al., "High-performance
+ * astrophysical visualization using Splotch" (ICCS 2010): every particle is a
+ * Gaussian density cut at f sigma (Section 2, first item), colour comes from
+ * a scalar through a palette (Section 2, third item), and the intensity along
+ * each line of sight obeys the transfer equation dI/dx = (E_p - A_p I) rho_p
+ * (Section 2, Eq. 1) for red, green and blue independently (Section 2,
+ * second item).  A frame is "process" (normalisation) then "display"
+ * (transform, colour, render) (Section 3.2).
+ *
+ * Conventions that the paper leaves open (camera model, pixel centres, the
+ * single-precision geometry that decides which pixels a particle reaches,
+ * normalisation, palette interpolation, ordering) are stated next to the
+ * call that applies them.
+ *
+ * Memory and streams.  Every pointer marked "device" is CUDA device memory
+ * owned by the caller; the library never allocates, frees or keeps a pointer
+ * beyond the call (the workspace is caller-owned too).  Inputs are read only.
+ * Every call that takes `stream` (a cudaStream_t passed as void*, NULL = the
+ * legacy default stream) only enqueues work and returns; results are ready
+ * when the stream reaches that point.  Calls return SPLOTCH_OK or a negative
+ * status; argument errors are reported before anything is enqueued.  Errors
+ * found on the device (for example a tile-entry capacity overflow) are
+ * written to a status word inside the workspace and reported by
+ * splotch_frame_info.  No call aborts, traps or throws.
+ */
+#ifndef SPLOTCH_H
+#define SPLOTCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPLOTCH_ABI_VERSION 1
+#define SPLOTCH_MAX_SPECIES 8
+#define SPLOTCH_MAX_PALETTE 256
+
+typedef enum {
+    SPLOTCH_OK = 0,
+    SPLOTCH_ERR_ARG = -1,         /* invalid argument, detected on the host */
+    SPLOTCH_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+    SPLOTCH_ERR_WORKSPACE = -3,   /* workspace too small (on the host) or tile entries over capacity (device) */
+    SPLOTCH_ERR_TIMEOUT = -4,     /* a bounded device wait ran out */
+    SPLOTCH_ERR_OOM_ADMISSION = -5,
+    SPLOTCH_ERR_STATE = -6        /* workspace does not hold the step this call needs */
+} splotch_status;
+
+typedef enum { SPLOTCH_F32 = 0, SPLOTCH_F16 = 1, SPLOTCH_BF16 = 2 } splotch_dtype;
+
+/* SPLOTCH_EMISSION: A = 0, I = sum_p E_p g_p, order-independent.
+ * SPLOTCH_ABSORPTIVE: Eq. 1 with per-species scalar A, front to back over
+ *   particles sorted by depth (ascending key, ties by ascending index).
+ * SPLOTCH_E_EQ_A: the paper's E = A setting (Section 2): I = 1 - exp(-sum_p E_p g_p). */
+typedef enum { SPLOTCH_EMISSION = 0, SPLOTCH_ABSORPTIVE = 1, SPLOTCH_E_EQ_A = 2 } splotch_mode;
+
+/* Particle block in structure-of-arrays form, one array per property, as in
+ * the block file layout of Section 3.1.  Species are contiguous index ranges
+ * [species_begin[s], species_begin[s+1]). */
+typedef struct {
+    uint64_t n;                 /* number of particles, < 2^32 */
+    const float *x, *y, *z;     /* device, n each: world position */
+    const float *h;             /* device, n: smoothing length */
+    const void *intensity;      /* device, n values of intensity_dtype: the scalar mapped to colour */
+    int32_t intensity_dtype;    /* splotch_dtype */
+    int32_t n_species;          /* 1..SPLOTCH_MAX_SPECIES */
+    uint64_t species_begin[SPLOTCH_MAX_SPECIES + 1];  /* host values; begin[0] = 0, begin[n_species] = n */
+} splotch_particles;
+
+/* Perspective camera.  The caller fills eye, target, up, fov_x_deg (full
+ * horizontal angle), width, height, znear; splotch_camera_init fills the rest. */
+typedef struct {
+    double eye[3], target[3], up[3];
+    double fov_x_deg;
+    int32_t width, height;
+    double znear;
+    double right[3], upv[3], fwd[3];   /* derived: right = up x fwd, upv = fwd x right */
+    double scale;                      /* derived: (width/2) / tan(fov/2), px per unit at unit depth */
+    double c_right, c_up, c_fwd;       /* derived: eye . right, eye . upv, eye . fwd */
+} splotch_camera;
+
+/* Palette: n_entries rgb triples (device, float, n_entries x 3), 2..256 entries. */
+typedef struct {
+    int32_t n_entries;
+    const float *rgb;
+} splotch_colormap;
+
+/* Render settings of one species (Section 2: E and A per particle, colour
+ * through a palette or fixed). */
+typedef struct {
+    int32_t use_log;         /* normalise log10(max(v, 1e-37)) instead of v */
+    int32_t use_colormap;    /* 1: palette(t); 0: fixed_rgb */
+    float lo, hi;            /* normalisation range; NaN = min/max over the species (computed on the device) */
+    float brightness;        /* E = brightness * colour */
+    float absorption;        /* A = absorption * (1, 1, 1); 0 = pure emission */
+    float fixed_rgb[3];
+} splotch_species;
+
+typedef struct {
+    int32_t mode;                 /* splotch_mode */
+    int32_t tile;                 /* screen tile side in px: 8, 16 or 32 */
+    float sigma_per_h;            /* sigma = sigma_per_h * h (default 1) */
+    float trunc_f;                /* footprint cut at f sigma (default 2) */
+    int32_t batch;                /* particles staged per renderer batch: 64, 128 or 256 */
+    int32_t large_threshold_px;   /* footprint area (px) above which a particle's tile entries are
+                                     emitted cooperatively; 0 = (width + height) / 2 (Section 3.2) */
+    uint64_t max_tile_entries;    /* capacity of the tile-entry arrays in the workspace, < 2^32 */
+} splotch_render_params;
+
+/* Result summary read back by splotch_frame_info (synchronises the stream). */
+typedef struct {
+    int32_t status;               /* device-side status (splotch_status) */
+    uint32_t visible;             /* V: particles that reach the image */
+    uint64_t tile_entries;        /* D: sum over visible particles of tiles touched */
+    uint32_t large;               /* particles sent to the cooperative emission path */
+    uint32_t ntiles;
+    float lo[SPLOTCH_MAX_SPECIES], hi[SPLOTCH_MAX_SPECIES];   /* normalisation range used */
+} splotch_frame_info_t;
+
+/* Library ABI version (SPLOTCH_ABI_VERSION). */
+int splotch_abi_version(void);
+
+/* Text for a status code; never NULL. */
+const char *splotch_status_string(int status);
+
+/*
+ * Fill the derived camera fields on the host in double precision.
+ * forward = normalize(target - eye), right = normalize(up x forward),
+ * upv = forward x right (right-handed, +y up on screen), scale =
+ * (width/2)/tan(fov_x/2).  Camera coordinates of p are X = p.right - c_right,
+ * Y = p.upv - c_up, Z = p.fwd - c_fwd.  SPLOTCH_ERR_ARG when target == eye,
+ * up is parallel to the view, fov is not in (0, 180), or a size is < 1.
+ */
+int splotch_camera_init(splotch_camera *cam);
+
+/*
+ * Bytes of workspace for up to n particles with this camera and parameters
+ * (tile size and max_tile_entries matter).  The workspace must be 256-byte
+ * aligned device memory.  One workspace serves one frame at a time.
+ */
+int splotch_workspace_size(uint64_t n, const splotch_camera *cam, const splotch_render_params *params,
+                           size_t *bytes);
+
+/*
+ * Transform (Section 3.2, "transformation into screen coordinates";
+ * footprint of Section 2, first item).  Per particle, in this order, each
+ * operation rounded separately:
+ *   Z  = fma(z, fwd2, fma(y, fwd1, x * fwd0)) - c_fwd          in double;
+ *        culled when Z <= znear; depth key = bit pattern of (float)Z
+ *   X  = fmaf(z, r2, fmaf(y, r1, x * r0)) - (float)c_right      in float (basis rounded to float), Y likewise
+ *   inv = 1 / (float)Z;  sx = W/2 + (s * X) * inv;  sy = H/2 - (s * Y) * inv    (s = (float)scale)
+ *   sigma_pix = (s * (sigma_per_h * h)) * inv;  r = trunc_f * sigma_pix;  r2 = r * r
+ *   box x0 = max(0, floor((sx - r) - 0.5)), x1 = min(W - 1, floor((sx + r) - 0.5) + 1), y likewise;
+ *       culled when empty or not finite
+ * Pixel (i, j) (centre (i + 0.5, j + 0.5), row 0 on top) receives the
+ * particle iff fmaf(dy, dy, dx * dx) < r2 with dx = (i + 0.5f) - sx,
+ * dy = (j + 0.5f) - sy; such a pixel always lies in the box.
+ * Writes the per-particle record, key and box into the workspace.
+ */
+int splotch_transform(const splotch_particles *p, const splotch_camera *cam, const splotch_render_params *params,
+                      void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Normalise and colour (Section 3.2 "normalizing of some
+ * particle values"; Section 2 colour look-up table).  species[s] applies to
+ * range s of p.  Per species, u = log10(max(v, 1e-37)) (use_log) or v;
+ * [lo, hi] = the given range, or min/max of u over every particle of the
+ * species when lo or hi is NaN; t = clamp((u - lo)/(hi - lo), 0, 1) (0 when
+ * hi == lo); palette value by linear interpolation, w = t (K - 1),
+ * k = min(floor(w), K - 2); E = brightness * colour (or * fixed_rgb),
+ * A = absorption.  Half-precision intensity is widened to float exactly.
+ */
+int splotch_colorize(const splotch_particles *p, const splotch_species *species, const splotch_colormap *cmap,
+                     void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Depth sort, tile binning and tile render into image
+ * (device, float, height x width x 3, row 0 on top).  Absorptive mode sorts
+ * visible particles by ascending key, ties by ascending index (a stable LSD
+ * radix sort); the other modes keep index order.  Binning lists, for every
+ * tile (row-major), the particles whose box meets it, in that order
+ * (bit-exact).  The render integrates Eq. 1 per pixel over its tile's list
+ * with g = exp(-d^2 / sigma_pix^2): emission sum E g; absorptive front to
+ * back C += T S, T *= exp(-A g), S = E (1 - exp(-A g)) / A (E g when A = 0);
+ * E = A: 1 - exp(-sum E g).  Background 0.  The same params as the
+ * transform call, and its particle count n, must be given.  Runs
+ * splotch_sort, splotch_bin and splotch_render_tiles in order.
+ */
+int splotch_render(const splotch_render_params *params, const splotch_camera *cam, uint64_t n, void *workspace,
+                   size_t workspace_bytes, float *image, void *stream);
+
+/* The three parts of splotch_render, callable one by one (same arguments). */
+int splotch_sort(const splotch_render_params *params, const splotch_camera *cam, uint64_t n, void *workspace,
+                 size_t workspace_bytes, void *stream);
+int splotch_bin(const splotch_render_params *params, const splotch_camera *cam, uint64_t n, void *workspace,
+                size_t workspace_bytes, void *stream);
+int splotch_render_tiles(const splotch_render_params *params, const splotch_camera *cam, uint64_t n,
+                         void *workspace, size_t workspace_bytes, float *image, void *stream);
+
+/* Synchronises `stream` and reads the frame summary from the workspace
+ * (written by the last transform/colorize/render on it). */
+int splotch_frame_info(const void *workspace, size_t workspace_bytes, splotch_frame_info_t *info, void *stream);
+
+/*
+ * Test access.  Each call synchronises `stream`, reads the workspace layout
+ * recorded by splotch_transform, then enqueues device-to-device copies.
+ * splotch_get_keys: key (n x uint32, 0xFFFFFFFF when culled) and box
+ *   (n x 4 int32: x0, y0, x1, y1; 0, 0, -1, -1 when culled); either may be NULL.
+ * splotch_get_geometry: sx, sy, r2 (n floats each; 0 when culled); any may be NULL.
+ * splotch_get_order: the V visible particle indices in render order.
+ * splotch_get_tile_lists: offsets (ntiles + 1 uint32) and list (capacity
+ *   uint32, first D used); SPLOTCH_ERR_WORKSPACE when capacity < D (read D first).
+ * splotch_get_colors: E and A (n x 4 floats: Er, Eg, Eb, A).
+ */
+int splotch_get_keys(const void *workspace, size_t workspace_bytes, uint32_t *key, int32_t *box, void *stream);
+int splotch_get_geometry(const void *workspace, size_t workspace_bytes, float *sx, float *sy, float *r2,
+                         void *stream);
+int splotch_get_order(const void *workspace, size_t workspace_bytes, uint32_t *order, void *stream);
+int splotch_get_tile_lists(const void *workspace, size_t workspace_bytes, uint32_t *offsets, uint32_t *list,
+                           uint64_t capacity, void *stream);
+int splotch_get_colors(const void *workspace, size_t workspace_bytes, float *ea, void *stream);
+
+/*
+ * Measurement helpers.
+ * splotch_count_fragments: enqueues a count, over the visible particles of
+ *   the last transform, of the (pixel, particle) pairs that pass the
+ *   membership test of splotch_transform (the fragments F of the frame);
+ *   writes one uint64 to `out` (device).  Not part of a frame.
+ * splotch_launch_count: kernels this library has launched in this process.
+ */
+int splotch_count_fragments(const splotch_render_params *params, const splotch_camera *cam, uint64_t n,
+                            void *workspace, size_t workspace_bytes, uint64_t *out, void *stream);
+uint64_t splotch_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPLOTCH_H */

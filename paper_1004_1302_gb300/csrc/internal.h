@@ -1,0 +1,145 @@
+// Internal declarations of the GB300 Splotch library: workspace layout,
+// device header and the launchers of each kernel file.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "splotch.h"
+
+namespace spl {
+
+constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
+constexpr uint32_t kMagic = 0x5350'4C54u;  // "SPLT"
+
+// Radix sort geometry: 256 threads x 16 items = one 4096-item tile per step.
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kRadix = 256;
+constexpr int kMaxSortCtas = 2048;
+
+// Byte offsets of every workspace section.  Sections that depend only on the
+// particle count come first, so colorize can find its output from n alone.
+struct Layout {
+    uint64_t n;
+    int32_t width, height, tile, ntx, nty;
+    uint32_t ntiles;
+    uint64_t cap;            // tile-entry capacity
+    uint32_t sort_ctas;      // CTAs of a radix pass over particles
+    uint32_t ent_ctas;       // CTAs of a radix pass over tile entries
+    uint32_t hist_ctas;      // max(sort_ctas, ent_ctas): rows of the histogram table
+    uint32_t pad0;
+    uint64_t off_geo, off_col, off_key, off_box;
+    uint64_t off_sk[2], off_sv[2];
+    uint64_t off_large, off_part;
+    uint64_t off_hist, off_htot;
+    uint64_t off_toff;
+    uint64_t off_ek[2], off_ev[2];
+    uint64_t total;
+};
+
+struct Header {
+    uint32_t magic;
+    int32_t status;
+    uint32_t visible;          // V
+    uint32_t n_large;
+    uint64_t tile_entries;     // D (may exceed cap on overflow)
+    uint32_t tile_entries32;   // min(D, cap), the count the entry sort works on
+    uint32_t key_min, key_max; // over visible particles
+    uint32_t sorted_buf;       // ping-pong buffer holding the ordered visible list
+    uint32_t n_species;
+    uint32_t mode;
+    uint32_t range_lo_enc[SPLOTCH_MAX_SPECIES];   // order-preserving encodings for atomic min/max
+    uint32_t range_hi_enc[SPLOTCH_MAX_SPECIES];
+    float lo[SPLOTCH_MAX_SPECIES], hi[SPLOTCH_MAX_SPECIES];
+    Layout layout;
+};
+
+constexpr uint64_t kHeaderBytes = 4096;
+static_assert(sizeof(Header) <= kHeaderBytes, "header too large");
+
+// Transform parameters in the form the kernels use (host computes once).
+struct TransformArgs {
+    const float *x, *y, *z, *h;
+    uint64_t n;
+    double fwd0, fwd1, fwd2, c_fwd, znear;
+    float r0, r1, r2, cr, u0, u1, u2, cu;
+    float s, half_w, half_h, w_max, h_max;
+    float sigma_per_h, trunc_f;
+};
+
+struct ColorizeArgs {
+    const void *v;
+    int dtype;
+    uint64_t n;
+    int n_species;
+    uint64_t begin[SPLOTCH_MAX_SPECIES + 1];
+    splotch_species sp[SPLOTCH_MAX_SPECIES];
+    const float *palette;
+    int n_entries;
+};
+
+// One radix pass: digit = ((key - kmin) >> shift) & mask.
+struct RadixPass {
+    const uint32_t *key_in;
+    const uint32_t *val_in;    // nullptr: value = item index (first pass over particles)
+    uint32_t *key_out, *val_out;
+    const uint32_t *n_dev;     // device item count (nullptr: n_host)
+    uint32_t n_host;
+    uint32_t shift, mask;
+    int depth_pass;            // >= 0: pass index of the depth sort (kmin from header, skip test); -1: plain
+    int skip_invalid;          // drop kInvalidKey items (first pass over particles)
+    uint32_t ctas;             // grid size of upsweep/downsweep
+    uint32_t *hist;            // [256][ctas] (row stride hist_ctas)
+    uint32_t hist_stride;
+    uint32_t *htot;            // [256]
+    Header *hdr;
+};
+
+struct BinArgs {
+    Header *hdr;
+    const uint32_t *list[2];   // ordered visible list candidates (sorted_buf selects)
+    const ushort4 *box;
+    uint64_t *part;            // per-CTA partial sums
+    uint32_t ctas;
+    uint32_t *ek, *ev;         // emitted entries (tile id, particle)
+    uint2 *large;              // (entry offset, particle) of large particles
+    uint64_t cap;
+    int tile, ntx;
+    uint32_t large_tiles;      // particles touching more tiles than this go to the cooperative path
+};
+
+struct RenderArgs {
+    const Header *hdr;
+    const uint32_t *toff;      // ntiles + 1
+    const uint32_t *list;      // tile-sorted particle indices
+    const float4 *geo;         // sx, sy, r2, -log2(e)/sigma_pix^2
+    const float4 *col;         // Er, Eg, Eb, A
+    float *image;
+    int width, height, tile, ntx, mode, batch;
+};
+
+// Layout of a workspace for n particles with this camera/params.
+int compute_layout(uint64_t n, int width, int height, int tile, uint64_t cap, Layout *out);
+
+inline Header *header(void *ws) { return reinterpret_cast<Header *>(ws); }
+template <class T> inline T *at(void *ws, uint64_t off) {
+    return reinterpret_cast<T *>(static_cast<char *>(ws) + off);
+}
+
+// Kernel launches made by this library (a process-wide counter).
+void count_launches(uint64_t k);
+
+// Launchers (each returns cudaGetLastError()).
+cudaError_t launch_init_header(void *ws, const Layout &L, int n_species, int mode, cudaStream_t st);
+cudaError_t launch_transform(const TransformArgs &a, void *ws, const Layout &L, cudaStream_t st);
+cudaError_t launch_colorize(const ColorizeArgs &a, void *ws, const Layout &L, cudaStream_t st);
+cudaError_t launch_sort(void *ws, const Layout &L, int mode, cudaStream_t st);
+cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st);
+cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStream_t st);
+cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float *image, cudaStream_t st);
+cudaError_t launch_count_fragments(void *ws, const Layout &L, uint64_t *out, cudaStream_t st);
+
+}  // namespace spl

@@ -1,0 +1,232 @@
+// Tile renderer: one CTA per screen tile, two horizontally adjacent pixels
+// per thread.  The tile's particle list is staged in batches into shared
+// memory (double-buffered asynchronous copies); each warp culls a batch
+// against its 16x4 (or 8x8) pixel block with one test per lane and a ballot,
+// then walks the surviving particles in list order.  Per pixel it evaluates
+// the truncated Gaussian footprint (Section 2, first item) and integrates
+// Eq. 1 (Section 2) across the particle layer:
+//   emission    C += E g
+//   absorptive  C += T_acc S, T_acc *= T, with T = exp(-A g),
+//               S = E (1 - T)/A = E g q(A g), q(y) = (1 - e^-y)/y
+//   E = A       C += E g, then I = 1 - exp(-C)
+// Packed f32x2 arithmetic does both pixels of a thread in one instruction.
+#include "internal.h"
+#include "device_util.cuh"
+
+namespace spl {
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// (1 - e^-y)/y = sum_k (-y)^k / (k+1)!, truncated after y^6: relative error
+// below y^7/8! (under 2e-7 for y <= 0.5).
+__device__ __forceinline__ float2 q_series(float2 y) {
+    float2 q = f2(1.0f / 5040.0f);
+    q = __ffma2_rn(q, y, f2(-1.0f / 720.0f));
+    q = __ffma2_rn(q, y, f2(1.0f / 120.0f));
+    q = __ffma2_rn(q, y, f2(-1.0f / 24.0f));
+    q = __ffma2_rn(q, y, f2(1.0f / 6.0f));
+    q = __ffma2_rn(q, y, f2(-0.5f));
+    q = __ffma2_rn(q, y, f2(1.0f));
+    return q;
+}
+
+template <int T, int MODE, int B>
+__global__ void __launch_bounds__(T * T / 2) k_render(RenderArgs a) {
+    constexpr int kThreads = T * T / 2;
+    constexpr int WX = T >= 16 ? 16 : 8;        // warp block width in pixels
+    constexpr int WY = 64 / WX;                 // warp block height
+    constexpr int kWarpCols = T / WX;
+    __shared__ __align__(16) float4 sgeo[2][B];
+    __shared__ __align__(16) float4 scol[2][B];
+
+    const int tile = blockIdx.x;
+    const int tx = tile % a.ntx, ty = tile / a.ntx;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wx0 = tx * T + (warp % kWarpCols) * WX, wy0 = ty * T + (warp / kWarpCols) * WY;
+    const int px0 = wx0 + 2 * (lane % (WX / 2)), py = wy0 + lane / (WX / 2);
+    const float2 cx = make_float2((float)px0 + 0.5f, (float)px0 + 1.5f);
+    const float cy = (float)py + 0.5f;
+    // pixel-centre box of this warp, for the cull test
+    const float xa = (float)wx0 + 0.5f, xb = (float)(wx0 + WX) - 0.5f;
+    const float ya = (float)wy0 + 0.5f, yb = (float)(wy0 + WY) - 0.5f;
+
+    float2 cr = f2(0.f), cg = f2(0.f), cb = f2(0.f), tacc = f2(1.f);
+
+    const bool ok = a.hdr->status == SPLOTCH_OK;
+    const uint32_t begin = ok ? a.toff[tile] : 0u, end = ok ? a.toff[tile + 1] : 0u;
+
+    auto stage = [&](int buf, uint32_t base) {
+        const uint32_t nb = min((uint32_t)B, end - base);
+        for (uint32_t j = threadIdx.x; j < nb; j += kThreads) {
+            const uint32_t p = a.list[base + j];
+            cp_async16(&sgeo[buf][j], &a.geo[p]);
+            cp_async16(&scol[buf][j], &a.col[p]);
+        }
+    };
+
+    if (begin < end) stage(0, begin);
+    cp_async_commit();
+    int buf = 0;
+    for (uint32_t base = begin; base < end; base += B, buf ^= 1) {
+        const uint32_t next = base + B;
+        if (next < end) stage(buf ^ 1, next);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const uint32_t nb = min((uint32_t)B, end - base);
+        for (uint32_t c = 0; c < nb; c += 32) {
+            bool keep = false;
+            if (c + lane < nb) {
+                const float4 g = sgeo[buf][c + lane];
+                const float qx = fminf(fmaxf(g.x, xa), xb), qy = fminf(fmaxf(g.y, ya), yb);
+                const float ddx = g.x - qx, ddy = g.y - qy;
+                // conservative: a pixel that passes the exact test is never culled
+                keep = ddx * ddx + ddy * ddy <= g.z * 1.0001f + 0.01f;
+            }
+            uint32_t mask = __ballot_sync(0xFFFFFFFFu, keep);
+            while (mask) {
+                const int j = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const float4 g = sgeo[buf][c + j];
+                const float4 e = scol[buf][c + j];
+                const float2 dx = __fadd2_rn(cx, f2(-g.x));
+                const float dy = __fadd_rn(cy, -g.y);
+                const float2 d2 = __ffma2_rn(f2(dy), f2(dy), __fmul2_rn(dx, dx));
+                const float2 arg = __fmul2_rn(d2, f2(g.w));
+                float2 w;
+                w.x = d2.x < g.z ? ex2_approx(arg.x) : 0.0f;
+                w.y = d2.y < g.z ? ex2_approx(arg.y) : 0.0f;
+                if (MODE == SPLOTCH_ABSORPTIVE) {
+                    const float2 y = __fmul2_rn(w, f2(e.w));
+                    float2 s, t;
+                    if (e.w <= 0.5f) {
+                        const float2 q = q_series(y);
+                        s = __fmul2_rn(w, q);
+                        t = __ffma2_rn(make_float2(-y.x, -y.y), q, f2(1.0f));
+                    } else {
+                        t.x = ex2_approx(-1.4426950408889634f * y.x);
+                        t.y = ex2_approx(-1.4426950408889634f * y.y);
+                        const float inva = 1.0f / e.w;
+                        s = __fmul2_rn(__fadd2_rn(f2(1.0f), make_float2(-t.x, -t.y)), f2(inva));
+                    }
+                    w = __fmul2_rn(tacc, s);
+                    tacc = __fmul2_rn(tacc, t);
+                }
+                cr = __ffma2_rn(w, f2(e.x), cr);
+                cg = __ffma2_rn(w, f2(e.y), cg);
+                cb = __ffma2_rn(w, f2(e.z), cb);
+            }
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+
+    if (MODE == SPLOTCH_E_EQ_A) {
+        cr = make_float2(-expm1f(-cr.x), -expm1f(-cr.y));
+        cg = make_float2(-expm1f(-cg.x), -expm1f(-cg.y));
+        cb = make_float2(-expm1f(-cb.x), -expm1f(-cb.y));
+    }
+    if (py < a.height) {
+        float *row = a.image + (size_t)py * a.width * 3;
+        if (px0 < a.width) {
+            row[3 * px0 + 0] = cr.x; row[3 * px0 + 1] = cg.x; row[3 * px0 + 2] = cb.x;
+        }
+        if (px0 + 1 < a.width) {
+            row[3 * px0 + 3] = cr.y; row[3 * px0 + 4] = cg.y; row[3 * px0 + 5] = cb.y;
+        }
+    }
+}
+
+template <int T, int MODE>
+static void launch_tb(const RenderArgs &a, int ntiles, cudaStream_t st) {
+    switch (a.batch) {
+    case 64: k_render<T, MODE, 64><<<ntiles, T * T / 2, 0, st>>>(a); break;
+    case 128: k_render<T, MODE, 128><<<ntiles, T * T / 2, 0, st>>>(a); break;
+    default: k_render<T, MODE, 256><<<ntiles, T * T / 2, 0, st>>>(a); break;
+    }
+}
+
+template <int T>
+static void launch_t(const RenderArgs &a, int ntiles, cudaStream_t st) {
+    switch (a.mode) {
+    case SPLOTCH_EMISSION: launch_tb<T, SPLOTCH_EMISSION>(a, ntiles, st); break;
+    case SPLOTCH_ABSORPTIVE: launch_tb<T, SPLOTCH_ABSORPTIVE>(a, ntiles, st); break;
+    default: launch_tb<T, SPLOTCH_E_EQ_A>(a, ntiles, st); break;
+    }
+}
+
+cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float *image, cudaStream_t st) {
+    int bits = 0;
+    while (bits < 32 && (1ull << bits) < (unsigned long long)L.ntiles) ++bits;
+    const int passes = (bits + 7) / 8;
+    RenderArgs a{};
+    a.hdr = header(ws);
+    a.toff = at<uint32_t>(ws, L.off_toff);
+    a.list = at<uint32_t>(ws, L.off_ev[passes & 1]);
+    a.geo = at<float4>(ws, L.off_geo);
+    a.col = at<float4>(ws, L.off_col);
+    a.image = image;
+    a.width = L.width;
+    a.height = L.height;
+    a.tile = L.tile;
+    a.ntx = L.ntx;
+    a.mode = mode;
+    a.batch = batch;
+    switch (L.tile) {
+    case 8: launch_t<8>(a, (int)L.ntiles, st); break;
+    case 32: launch_t<32>(a, (int)L.ntiles, st); break;
+    default: launch_t<16>(a, (int)L.ntiles, st); break;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Number of (pixel, particle) pairs that pass the membership test, summed
+// over the visible particles (a measurement helper, not part of a frame).
+__global__ void __launch_bounds__(256) k_count_fragments(const float4 *geo, const ushort4 *box, const uint32_t *key,
+                                                         uint64_t n, unsigned long long *out) {
+    unsigned long long cnt = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (key[i] == kInvalidKey) continue;
+        const float4 g = geo[i];
+        const ushort4 b = box[i];
+        for (int j = b.y; j <= b.w; ++j) {
+            const float dy = __fsub_rn((float)j + 0.5f, g.y);
+            for (int x = b.x; x <= b.z; ++x) {
+                const float dx = __fsub_rn((float)x + 0.5f, g.x);
+                cnt += __fmaf_rn(dy, dy, __fmul_rn(dx, dx)) < g.z;
+            }
+        }
+    }
+    cnt = __reduce_add_sync(0xFFFFFFFFu, (unsigned)(cnt & 0xFFFFFFFFu)) +
+          ((unsigned long long)__reduce_add_sync(0xFFFFFFFFu, (unsigned)(cnt >> 32)) << 32);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, cnt);
+}
+
+cudaError_t launch_count_fragments(void *ws, const Layout &L, uint64_t *out, cudaStream_t st) {
+    cudaMemsetAsync(out, 0, sizeof(uint64_t), st);
+    if (L.n) {
+        k_count_fragments<<<1024, 256, 0, st>>>(at<float4>(ws, L.off_geo), at<ushort4>(ws, L.off_box),
+                                                at<uint32_t>(ws, L.off_key), L.n,
+                                                reinterpret_cast<unsigned long long *>(out));
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace spl

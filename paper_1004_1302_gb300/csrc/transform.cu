@@ -1,0 +1,241 @@
+// Transform (camera, depth key, screen footprint, tile box) and colorize
+// (range pre-pass, palette lookup) kernels.  Paper: Section 3.2 "process"
+// and "display"; Section 2 for the footprint and colour.
+#include "internal.h"
+#include "device_util.cuh"
+
+namespace spl {
+
+__global__ void k_init_header(Header *hdr, Layout L, int n_species, int mode) {
+    if (threadIdx.x != 0) return;
+    hdr->magic = kMagic;
+    hdr->status = SPLOTCH_OK;
+    hdr->visible = 0;
+    hdr->n_large = 0;
+    hdr->tile_entries = 0;
+    hdr->tile_entries32 = 0;
+    hdr->key_min = kInvalidKey;
+    hdr->key_max = 0;
+    hdr->sorted_buf = 0;
+    hdr->n_species = (uint32_t)n_species;
+    hdr->mode = (uint32_t)mode;
+    for (int s = 0; s < SPLOTCH_MAX_SPECIES; ++s) {
+        hdr->range_lo_enc[s] = 0xFFFFFFFFu;
+        hdr->range_hi_enc[s] = 0u;
+        hdr->lo[s] = 0.0f;
+        hdr->hi[s] = 0.0f;
+    }
+    hdr->layout = L;
+}
+
+struct Footprint {
+    float4 geo;      // sx, sy, r2, -log2(e)/sigma_pix^2
+    uint32_t key;    // kInvalidKey when culled
+    ushort4 box;     // x0, y0, x1, y1
+};
+
+// The single-precision geometry of the transform call, operation by
+// operation, each rounded on its own (no contraction).
+__device__ __forceinline__ Footprint footprint(const TransformArgs &a, float x, float y, float z, float h) {
+    Footprint f;
+    f.geo = make_float4(0.f, 0.f, 0.f, 0.f);
+    f.key = kInvalidKey;
+    f.box = make_ushort4(1, 1, 0, 0);
+    double Z = __dsub_rn(__fma_rn((double)z, a.fwd2, __fma_rn((double)y, a.fwd1, __dmul_rn((double)x, a.fwd0))),
+                         a.c_fwd);
+    if (!(Z > a.znear)) return f;
+    float Zf = __double2float_rn(Z);
+    float X = __fsub_rn(__fmaf_rn(z, a.r2, __fmaf_rn(y, a.r1, __fmul_rn(x, a.r0))), a.cr);
+    float Y = __fsub_rn(__fmaf_rn(z, a.u2, __fmaf_rn(y, a.u1, __fmul_rn(x, a.u0))), a.cu);
+    float inv = __frcp_rn(Zf);
+    float px = __fadd_rn(a.half_w, __fmul_rn(__fmul_rn(a.s, X), inv));
+    float py = __fsub_rn(a.half_h, __fmul_rn(__fmul_rn(a.s, Y), inv));
+    float sg = __fmul_rn(__fmul_rn(a.s, __fmul_rn(a.sigma_per_h, h)), inv);
+    float r = __fmul_rn(a.trunc_f, sg);
+    float lx = floorf(__fsub_rn(__fsub_rn(px, r), 0.5f));
+    float hx = __fadd_rn(floorf(__fsub_rn(__fadd_rn(px, r), 0.5f)), 1.0f);
+    float ly = floorf(__fsub_rn(__fsub_rn(py, r), 0.5f));
+    float hy = __fadd_rn(floorf(__fsub_rn(__fadd_rn(py, r), 0.5f)), 1.0f);
+    float x0 = lx > 0.0f ? lx : 0.0f, x1 = hx < a.w_max ? hx : a.w_max;
+    float y0 = ly > 0.0f ? ly : 0.0f, y1 = hy < a.h_max ? hy : a.h_max;
+    if (!(lx <= hx) || !(ly <= hy) || !(x0 <= x1) || !(y0 <= y1)) return f;
+    f.key = __float_as_uint(Zf);
+    f.geo = make_float4(px, py, __fmul_rn(r, r), __fdiv_rn(-1.4426950408889634f, __fmul_rn(sg, sg)));
+    f.box = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
+    return f;
+}
+
+template <int kVec>
+__global__ void __launch_bounds__(256) k_transform(TransformArgs a, float4 *geo, uint32_t *key, ushort4 *box,
+                                                   Header *hdr) {
+    uint32_t nvis = 0, kmin = kInvalidKey, kmax = 0;
+    const uint64_t nvec = (a.n + kVec - 1) / kVec;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nvec;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i0 = t * kVec;
+        float xs[kVec], ys[kVec], zs[kVec], hs[kVec];
+        if (kVec == 4 && i0 + 4 <= a.n) {
+            float4 vx = __ldg(reinterpret_cast<const float4 *>(a.x) + t);
+            float4 vy = __ldg(reinterpret_cast<const float4 *>(a.y) + t);
+            float4 vz = __ldg(reinterpret_cast<const float4 *>(a.z) + t);
+            float4 vh = __ldg(reinterpret_cast<const float4 *>(a.h) + t);
+            xs[0] = vx.x; xs[1 % kVec] = vx.y; xs[2 % kVec] = vx.z; xs[3 % kVec] = vx.w;
+            ys[0] = vy.x; ys[1 % kVec] = vy.y; ys[2 % kVec] = vy.z; ys[3 % kVec] = vy.w;
+            zs[0] = vz.x; zs[1 % kVec] = vz.y; zs[2 % kVec] = vz.z; zs[3 % kVec] = vz.w;
+            hs[0] = vh.x; hs[1 % kVec] = vh.y; hs[2 % kVec] = vh.z; hs[3 % kVec] = vh.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kVec; ++k) {
+                uint64_t i = i0 + k < a.n ? i0 + k : a.n - 1;
+                xs[k] = __ldg(a.x + i); ys[k] = __ldg(a.y + i); zs[k] = __ldg(a.z + i); hs[k] = __ldg(a.h + i);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kVec; ++k) {
+            const uint64_t i = i0 + k;
+            if (i >= a.n) break;
+            Footprint f = footprint(a, xs[k], ys[k], zs[k], hs[k]);
+            geo[i] = f.geo;
+            key[i] = f.key;
+            box[i] = f.box;
+            if (f.key != kInvalidKey) {
+                nvis += 1;
+                kmin = min(kmin, f.key);
+                kmax = max(kmax, f.key);
+            }
+        }
+    }
+    nvis = __reduce_add_sync(0xFFFFFFFFu, nvis);
+    kmin = __reduce_min_sync(0xFFFFFFFFu, kmin);
+    kmax = __reduce_max_sync(0xFFFFFFFFu, kmax);
+    if (lane_id() == 0 && nvis) {
+        atomicAdd(&hdr->visible, nvis);
+        atomicMin(&hdr->key_min, kmin);
+        atomicMax(&hdr->key_max, kmax);
+    }
+}
+
+// Range pre-pass of one species: min/max of u (log10 of the value, or the
+// value) into the header's order-preserving slots.
+__global__ void __launch_bounds__(256) k_range(const void *v, int dtype, uint64_t begin, uint64_t end, int use_log,
+                                               Header *hdr, int s) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (uint64_t i = begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < end;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        float u = load_value(v, dtype, i);
+        if (use_log) u = log10f(fmaxf(u, 1e-37f));
+        lo = fminf(lo, u);
+        hi = fmaxf(hi, u);
+    }
+    uint32_t elo = __reduce_min_sync(0xFFFFFFFFu, float_to_ordered(lo));
+    uint32_t ehi = __reduce_max_sync(0xFFFFFFFFu, float_to_ordered(hi));
+    if (lane_id() == 0) {
+        atomicMin(&hdr->range_lo_enc[s], elo);
+        atomicMax(&hdr->range_hi_enc[s], ehi);
+    }
+}
+
+__global__ void k_range_finish(Header *hdr, ColorizeArgs a) {
+    int s = threadIdx.x;
+    if (s >= a.n_species) return;
+    float lo = a.sp[s].lo, hi = a.sp[s].hi;
+    bool empty = a.begin[s + 1] == a.begin[s];
+    if (isnan(lo)) lo = empty ? 0.0f : ordered_to_float(hdr->range_lo_enc[s]);
+    if (isnan(hi)) hi = empty ? 0.0f : ordered_to_float(hdr->range_hi_enc[s]);
+    hdr->lo[s] = lo;
+    hdr->hi[s] = hi;
+}
+
+__global__ void __launch_bounds__(256) k_colorize(ColorizeArgs a, const Header *hdr, float4 *col) {
+    __shared__ float pal[SPLOTCH_MAX_PALETTE * 3];
+    for (int k = threadIdx.x; k < a.n_entries * 3; k += blockDim.x) pal[k] = a.palette[k];
+    __syncthreads();
+    const float kmax = (float)(a.n_entries - 1);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += (uint64_t)gridDim.x * blockDim.x) {
+        int s = 0;
+#pragma unroll 1
+        while (s + 1 < a.n_species && i >= a.begin[s + 1]) ++s;
+        const splotch_species &sp = a.sp[s];
+        float r, g, b;
+        if (sp.use_colormap) {
+            float u = load_value(a.v, a.dtype, i);
+            if (sp.use_log) u = log10f(fmaxf(u, 1e-37f));
+            const float lo = hdr->lo[s], hi = hdr->hi[s];
+            float t = hi > lo ? __fdiv_rn(u - lo, hi - lo) : 0.0f;
+            t = fminf(fmaxf(t, 0.0f), 1.0f);
+            float w = t * kmax;
+            int k = min((int)floorf(w), a.n_entries - 2);
+            float fr = w - (float)k;
+            r = (1.0f - fr) * pal[3 * k + 0] + fr * pal[3 * k + 3];
+            g = (1.0f - fr) * pal[3 * k + 1] + fr * pal[3 * k + 4];
+            b = (1.0f - fr) * pal[3 * k + 2] + fr * pal[3 * k + 5];
+        } else {
+            r = sp.fixed_rgb[0]; g = sp.fixed_rgb[1]; b = sp.fixed_rgb[2];
+        }
+        col[i] = make_float4(sp.brightness * r, sp.brightness * g, sp.brightness * b, sp.absorption);
+    }
+}
+
+static int sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 148;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 148;
+    }
+    return cached[dev];
+}
+
+cudaError_t launch_init_header(void *ws, const Layout &L, int n_species, int mode, cudaStream_t st) {
+    k_init_header<<<1, 32, 0, st>>>(header(ws), L, n_species, mode);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transform(const TransformArgs &a, void *ws, const Layout &L, cudaStream_t st) {
+    if (a.n == 0) return cudaGetLastError();
+    const bool aligned = ((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.y) |
+                           reinterpret_cast<uintptr_t>(a.z) | reinterpret_cast<uintptr_t>(a.h)) & 15u) == 0;
+    const int sms = sm_count();
+    float4 *geo = at<float4>(ws, L.off_geo);
+    uint32_t *key = at<uint32_t>(ws, L.off_key);
+    ushort4 *box = at<ushort4>(ws, L.off_box);
+    if (aligned) {
+        uint64_t blocks = (a.n + 4 * 256 - 1) / (4 * 256);
+        int grid = (int)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);
+        k_transform<4><<<grid, 256, 0, st>>>(a, geo, key, box, header(ws));
+    } else {
+        uint64_t blocks = (a.n + 255) / 256;
+        int grid = (int)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);
+        k_transform<1><<<grid, 256, 0, st>>>(a, geo, key, box, header(ws));
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colorize(const ColorizeArgs &a, void *ws, const Layout &L, cudaStream_t st) {
+    const int sms = sm_count();
+    for (int s = 0; s < a.n_species; ++s) {
+        const splotch_species &sp = a.sp[s];
+        const uint64_t b = a.begin[s], e = a.begin[s + 1];
+        if (e <= b || !(isnan(sp.lo) || isnan(sp.hi))) continue;
+        uint64_t blocks = (e - b + 255) / 256;
+        int grid = (int)(blocks < (uint64_t)sms * 4 ? blocks : (uint64_t)sms * 4);
+        k_range<<<grid, 256, 0, st>>>(a.v, a.dtype, b, e, sp.use_log, header(ws), s);
+        count_launches(1);
+    }
+    k_range_finish<<<1, 32, 0, st>>>(header(ws), a);
+    count_launches(1);
+    if (a.n) {
+        uint64_t blocks = (a.n + 255) / 256;
+        int grid = (int)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);
+        k_colorize<<<grid, 256, 0, st>>>(a, header(ws), at<float4>(ws, L.off_col));
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace spl

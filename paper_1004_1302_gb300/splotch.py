@@ -1,0 +1,456 @@
+"""ctypes binding of the C ABI in ``include/splotch.h``.
+
+Argument marshalling only: every step of a frame runs in the CUDA library
+``_splotch.so`` (built in-tree by :func:`build`).  PyTorch provides device
+memory and streams.  Importing this module never falls back to anything
+else: if the library is missing or fails to load, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass, field
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_CSRC = os.path.join(_HERE, "csrc")
+_INCLUDE = os.path.join(_ROOT, "include")
+LIB_PATH = os.path.join(_HERE, "_splotch.so")
+SOURCES = ["splotch_api.cu", "transform.cu", "sort.cu", "bin.cu", "render.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+OK, ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_TIMEOUT, ERR_OOM_ADMISSION, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+F32, F16, BF16 = 0, 1, 2
+EMISSION, ABSORPTIVE, E_EQ_A = 0, 1, 2
+MAX_SPECIES = 8
+
+
+def _nvcc() -> str:
+    for p in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc"):
+        if p and os.path.exists(p):
+            return p
+    return "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA sources for sm_103a (one object per file, in
+    parallel) and link ``_splotch.so`` next to this file."""
+    srcs = [os.path.join(_CSRC, s) for s in SOURCES]
+    deps = srcs + [os.path.join(_CSRC, "internal.h"), os.path.join(_CSRC, "device_util.cuh"),
+                   os.path.join(_INCLUDE, "splotch.h")]
+    if not force and os.path.exists(LIB_PATH):
+        t = os.path.getmtime(LIB_PATH)
+        if all(os.path.getmtime(d) <= t for d in deps):
+            return LIB_PATH
+    objdir = os.path.join(_HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    common = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
+              "-I", _INCLUDE, "-I", _CSRC]
+
+    def compile_one(src):
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        cmd = common + ["-c", src, "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
+        if verbose and r.stderr:
+            print(r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+        objs = list(ex.map(compile_one, srcs))
+    tmp = LIB_PATH + ".tmp"
+    r = subprocess.run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+# --- structs (mirror include/splotch.h) -------------------------------------
+
+class Particles(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("h", ctypes.c_void_p), ("intensity", ctypes.c_void_p), ("intensity_dtype", ctypes.c_int32),
+                ("n_species", ctypes.c_int32), ("species_begin", ctypes.c_uint64 * (MAX_SPECIES + 1))]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_double * 3), ("target", ctypes.c_double * 3), ("up", ctypes.c_double * 3),
+                ("fov_x_deg", ctypes.c_double), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("znear", ctypes.c_double), ("right", ctypes.c_double * 3), ("upv", ctypes.c_double * 3),
+                ("fwd", ctypes.c_double * 3), ("scale", ctypes.c_double), ("c_right", ctypes.c_double),
+                ("c_up", ctypes.c_double), ("c_fwd", ctypes.c_double)]
+
+
+class Colormap(ctypes.Structure):
+    _fields_ = [("n_entries", ctypes.c_int32), ("rgb", ctypes.c_void_p)]
+
+
+class SpeciesParams(ctypes.Structure):
+    _fields_ = [("use_log", ctypes.c_int32), ("use_colormap", ctypes.c_int32), ("lo", ctypes.c_float),
+                ("hi", ctypes.c_float), ("brightness", ctypes.c_float), ("absorption", ctypes.c_float),
+                ("fixed_rgb", ctypes.c_float * 3)]
+
+
+class RenderParams(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("tile", ctypes.c_int32), ("sigma_per_h", ctypes.c_float),
+                ("trunc_f", ctypes.c_float), ("batch", ctypes.c_int32), ("large_threshold_px", ctypes.c_int32),
+                ("max_tile_entries", ctypes.c_uint64)]
+
+
+class FrameInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("visible", ctypes.c_uint32), ("tile_entries", ctypes.c_uint64),
+                ("large", ctypes.c_uint32), ("ntiles", ctypes.c_uint32), ("lo", ctypes.c_float * MAX_SPECIES),
+                ("hi", ctypes.c_float * MAX_SPECIES)]
+
+
+EXPORTS = ["splotch_abi_version", "splotch_status_string", "splotch_camera_init", "splotch_workspace_size",
+           "splotch_transform", "splotch_colorize", "splotch_render", "splotch_sort", "splotch_bin",
+           "splotch_render_tiles", "splotch_frame_info", "splotch_get_keys", "splotch_get_geometry",
+           "splotch_get_order", "splotch_get_tile_lists", "splotch_get_colors", "splotch_count_fragments",
+           "splotch_launch_count"]
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} is missing; run paper_1004_1302_gb300.splotch.build()")
+    lib = ctypes.CDLL(p)
+    V, P, U64, I32 = ctypes.c_void_p, ctypes.POINTER, ctypes.c_uint64, ctypes.c_int
+    sig = {
+        "splotch_abi_version": ([], I32),
+        "splotch_status_string": ([I32], ctypes.c_char_p),
+        "splotch_camera_init": ([P(Camera)], I32),
+        "splotch_workspace_size": ([U64, P(Camera), P(RenderParams), P(ctypes.c_size_t)], I32),
+        "splotch_transform": ([P(Particles), P(Camera), P(RenderParams), V, ctypes.c_size_t, V], I32),
+        "splotch_colorize": ([P(Particles), P(SpeciesParams), P(Colormap), V, ctypes.c_size_t, V], I32),
+        "splotch_render": ([P(RenderParams), P(Camera), U64, V, ctypes.c_size_t, V, V], I32),
+        "splotch_sort": ([P(RenderParams), P(Camera), U64, V, ctypes.c_size_t, V], I32),
+        "splotch_bin": ([P(RenderParams), P(Camera), U64, V, ctypes.c_size_t, V], I32),
+        "splotch_render_tiles": ([P(RenderParams), P(Camera), U64, V, ctypes.c_size_t, V, V], I32),
+        "splotch_frame_info": ([V, ctypes.c_size_t, P(FrameInfo), V], I32),
+        "splotch_get_keys": ([V, ctypes.c_size_t, V, V, V], I32),
+        "splotch_get_geometry": ([V, ctypes.c_size_t, V, V, V, V], I32),
+        "splotch_get_order": ([V, ctypes.c_size_t, V, V], I32),
+        "splotch_get_tile_lists": ([V, ctypes.c_size_t, V, V, U64, V], I32),
+        "splotch_get_colors": ([V, ctypes.c_size_t, V, V], I32),
+        "splotch_count_fragments": ([P(RenderParams), P(Camera), U64, V, ctypes.c_size_t, V, V], I32),
+        "splotch_launch_count": ([], U64),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class SplotchError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().splotch_status_string(status).decode()
+        super().__init__(f"{where}: {msg} ({status})")
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise SplotchError(status, where)
+
+
+# --- same-name wrappers -------------------------------------------------------
+
+def splotch_camera_init(cam: Camera) -> Camera:
+    _check(load().splotch_camera_init(ctypes.byref(cam)), "splotch_camera_init")
+    return cam
+
+
+def splotch_workspace_size(n: int, cam: Camera, params: RenderParams) -> int:
+    out = ctypes.c_size_t()
+    _check(load().splotch_workspace_size(n, ctypes.byref(cam), ctypes.byref(params), ctypes.byref(out)),
+           "splotch_workspace_size")
+    return out.value
+
+
+def splotch_transform(p: Particles, cam: Camera, params: RenderParams, ws: int, ws_bytes: int, stream: int):
+    _check(load().splotch_transform(ctypes.byref(p), ctypes.byref(cam), ctypes.byref(params), ws, ws_bytes, stream),
+           "splotch_transform")
+
+
+def splotch_colorize(p: Particles, species, cmap: Colormap, ws: int, ws_bytes: int, stream: int):
+    arr = (SpeciesParams * MAX_SPECIES)(*species)
+    _check(load().splotch_colorize(ctypes.byref(p), arr, ctypes.byref(cmap), ws, ws_bytes, stream),
+           "splotch_colorize")
+
+
+def splotch_render(params: RenderParams, cam: Camera, n: int, ws: int, ws_bytes: int, image: int, stream: int):
+    _check(load().splotch_render(ctypes.byref(params), ctypes.byref(cam), n, ws, ws_bytes, image, stream),
+           "splotch_render")
+
+
+def splotch_sort(params, cam, n, ws, ws_bytes, stream):
+    _check(load().splotch_sort(ctypes.byref(params), ctypes.byref(cam), n, ws, ws_bytes, stream), "splotch_sort")
+
+
+def splotch_bin(params, cam, n, ws, ws_bytes, stream):
+    _check(load().splotch_bin(ctypes.byref(params), ctypes.byref(cam), n, ws, ws_bytes, stream), "splotch_bin")
+
+
+def splotch_render_tiles(params, cam, n, ws, ws_bytes, image, stream):
+    _check(load().splotch_render_tiles(ctypes.byref(params), ctypes.byref(cam), n, ws, ws_bytes, image, stream),
+           "splotch_render_tiles")
+
+
+def splotch_frame_info(ws: int, ws_bytes: int, stream: int) -> FrameInfo:
+    info = FrameInfo()
+    _check(load().splotch_frame_info(ws, ws_bytes, ctypes.byref(info), stream), "splotch_frame_info")
+    return info
+
+
+def splotch_get_keys(ws, ws_bytes, key_ptr, box_ptr, stream):
+    _check(load().splotch_get_keys(ws, ws_bytes, key_ptr, box_ptr, stream), "splotch_get_keys")
+
+
+def splotch_get_geometry(ws, ws_bytes, sx, sy, r2, stream):
+    _check(load().splotch_get_geometry(ws, ws_bytes, sx, sy, r2, stream), "splotch_get_geometry")
+
+
+def splotch_get_order(ws, ws_bytes, order, stream):
+    _check(load().splotch_get_order(ws, ws_bytes, order, stream), "splotch_get_order")
+
+
+def splotch_get_tile_lists(ws, ws_bytes, offsets, lst, capacity, stream):
+    _check(load().splotch_get_tile_lists(ws, ws_bytes, offsets, lst, capacity, stream), "splotch_get_tile_lists")
+
+
+def splotch_get_colors(ws, ws_bytes, ea, stream):
+    _check(load().splotch_get_colors(ws, ws_bytes, ea, stream), "splotch_get_colors")
+
+
+def splotch_count_fragments(params, cam, n, ws, ws_bytes, out, stream):
+    _check(load().splotch_count_fragments(ctypes.byref(params), ctypes.byref(cam), n, ws, ws_bytes, out, stream),
+           "splotch_count_fragments")
+
+
+def splotch_launch_count() -> int:
+    return int(load().splotch_launch_count())
+
+
+# --- marshalling helpers ------------------------------------------------------
+
+def make_camera(spec) -> Camera:
+    """Camera struct from a spec with eye/target/up/fov_x_deg/width/height/znear."""
+    c = Camera()
+    c.eye[:] = [float(v) for v in spec.eye]
+    c.target[:] = [float(v) for v in spec.target]
+    c.up[:] = [float(v) for v in spec.up]
+    c.fov_x_deg = float(spec.fov_x_deg)
+    c.width, c.height = int(spec.width), int(spec.height)
+    c.znear = float(getattr(spec, "znear", 1e-3))
+    return splotch_camera_init(c)
+
+
+def make_species(sp) -> SpeciesParams:
+    s = SpeciesParams()
+    s.use_log = int(sp.use_log)
+    s.use_colormap = int(sp.use_colormap)
+    s.lo = float(sp.lo)
+    s.hi = float(sp.hi)
+    s.brightness = float(sp.brightness)
+    s.absorption = float(sp.absorption)
+    s.fixed_rgb[:] = [float(v) for v in sp.fixed_rgb]
+    return s
+
+
+def make_params(mode: int, tile: int = 16, batch: int = 128, sigma_per_h: float = 1.0, trunc_f: float = 2.0,
+                large_threshold_px: int = 0, max_tile_entries: int = 0) -> RenderParams:
+    p = RenderParams()
+    p.mode, p.tile, p.batch = int(mode), int(tile), int(batch)
+    p.sigma_per_h, p.trunc_f = float(sigma_per_h), float(trunc_f)
+    p.large_threshold_px = int(large_threshold_px)
+    p.max_tile_entries = int(max_tile_entries)
+    return p
+
+
+_DTYPE_CODE = {"f32": F32, "f16": F16, "bf16": BF16}
+
+
+@dataclass
+class DeviceParticles:
+    """A particle set resident on the device (torch tensors) and its species."""
+    x: object
+    y: object
+    z: object
+    h: object
+    v: object
+    dtype: str
+    species: list = field(default_factory=list)
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    def struct(self) -> Particles:
+        p = Particles()
+        p.n = self.n
+        p.x, p.y, p.z, p.h = (t.data_ptr() if self.n else None for t in (self.x, self.y, self.z, self.h))
+        p.intensity = self.v.data_ptr() if self.n else None
+        p.intensity_dtype = _DTYPE_CODE[self.dtype]
+        p.n_species = len(self.species)
+        for k, s in enumerate(self.species):
+            p.species_begin[k] = int(s.begin)
+        p.species_begin[len(self.species)] = self.n
+        return p
+
+
+def upload(ps, device="cuda", dtype: str = "f32", stream=None) -> DeviceParticles:
+    """Copy a host ParticleSet (numpy float32 arrays) to the device; the
+    intensity is stored as f32, f16 or bf16 (round to nearest even)."""
+    import torch
+    tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[dtype]
+    cols = [torch.from_numpy(a).to(device, non_blocking=False) for a in (ps.x, ps.y, ps.z, ps.h)]
+    v = torch.from_numpy(ps.v).to(device).to(tdt)
+    return DeviceParticles(*cols, v, dtype, list(ps.species))
+
+
+def rounded_intensity(ps, dtype: str):
+    """The intensity values exactly as the device holds them (float64 numpy)."""
+    import numpy as np
+    import torch
+    if dtype == "f32":
+        return ps.v.astype(np.float64)
+    tdt = {"f16": torch.float16, "bf16": torch.bfloat16}[dtype]
+    return torch.from_numpy(ps.v).to(tdt).to(torch.float64).numpy()
+
+
+class Frame:
+    """One frame's device state: workspace, palette and image buffers, and the
+    structs passed to the C calls.  Grows the tile-entry capacity when a frame
+    reports an overflow."""
+
+    def __init__(self, dp: DeviceParticles, cam_spec, palette, mode: int, tile: int = 16, batch: int = 128,
+                 sigma_per_h: float = 1.0, trunc_f: float = 2.0, large_threshold_px: int = 0,
+                 max_tile_entries: int | None = None, device="cuda"):
+        import torch
+        self.torch = torch
+        self.dp = dp
+        self.device = torch.device(device)
+        self.cam = make_camera(cam_spec)
+        self.W, self.H = int(cam_spec.width), int(cam_spec.height)
+        pal = torch.as_tensor(palette, dtype=torch.float32).reshape(-1, 3).contiguous()
+        self.palette = pal.to(self.device)
+        self.cmap = Colormap(int(pal.shape[0]), self.palette.data_ptr())
+        if max_tile_entries is None:
+            ntiles = math.ceil(self.W / tile) * math.ceil(self.H / tile)
+            max_tile_entries = max(4 * dp.n, 1024) + ntiles
+        self.params = make_params(mode, tile, batch, sigma_per_h, trunc_f, large_threshold_px, max_tile_entries)
+        self.pstruct = dp.struct()
+        self.species = [make_species(s) for s in dp.species]
+        self.image = torch.zeros((self.H, self.W, 3), dtype=torch.float32, device=self.device)
+        self._alloc()
+
+    def _alloc(self):
+        self.ws_bytes = splotch_workspace_size(self.dp.n, self.cam, self.params)
+        self.ws = self.torch.empty(self.ws_bytes, dtype=self.torch.uint8, device=self.device)
+
+    def stream_ptr(self, stream=None) -> int:
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device)
+        return s.cuda_stream
+
+    def transform(self, stream=None):
+        splotch_transform(self.pstruct, self.cam, self.params, self.ws.data_ptr(), self.ws_bytes,
+                          self.stream_ptr(stream))
+
+    def colorize(self, stream=None):
+        splotch_colorize(self.pstruct, self.species, self.cmap, self.ws.data_ptr(), self.ws_bytes,
+                         self.stream_ptr(stream))
+
+    def sort(self, stream=None):
+        splotch_sort(self.params, self.cam, self.dp.n, self.ws.data_ptr(), self.ws_bytes, self.stream_ptr(stream))
+
+    def bin(self, stream=None):
+        splotch_bin(self.params, self.cam, self.dp.n, self.ws.data_ptr(), self.ws_bytes, self.stream_ptr(stream))
+
+    def render_tiles(self, stream=None):
+        splotch_render_tiles(self.params, self.cam, self.dp.n, self.ws.data_ptr(), self.ws_bytes,
+                             self.image.data_ptr(), self.stream_ptr(stream))
+
+    def run(self, stream=None):
+        """Enqueue a whole frame (no host synchronisation)."""
+        self.transform(stream)
+        self.colorize(stream)
+        splotch_render(self.params, self.cam, self.dp.n, self.ws.data_ptr(), self.ws_bytes, self.image.data_ptr(),
+                       self.stream_ptr(stream))
+
+    def info(self, stream=None) -> FrameInfo:
+        return splotch_frame_info(self.ws.data_ptr(), self.ws_bytes, self.stream_ptr(stream))
+
+    def render(self, stream=None, max_retries: int = 3):
+        """Run a frame, grow the tile-entry capacity on overflow, and return the image."""
+        for _ in range(max_retries + 1):
+            self.run(stream)
+            inf = self.info(stream)
+            if inf.status == OK:
+                return self.image
+            if inf.status != ERR_WORKSPACE:
+                raise SplotchError(inf.status, "frame")
+            self.params.max_tile_entries = int(inf.tile_entries * 1.1) + 1024
+            self.ws = None
+            self._alloc()
+        raise SplotchError(ERR_WORKSPACE, "frame")
+
+    # test access
+    def keys(self):
+        t = self.torch
+        key = t.empty(self.dp.n, dtype=t.int32, device=self.device)
+        box = t.empty((self.dp.n, 4), dtype=t.int32, device=self.device)
+        splotch_get_keys(self.ws.data_ptr(), self.ws_bytes, key.data_ptr() if self.dp.n else None,
+                         box.data_ptr() if self.dp.n else None, self.stream_ptr())
+        return key, box
+
+    def geometry(self):
+        t = self.torch
+        out = [t.empty(self.dp.n, dtype=t.float32, device=self.device) for _ in range(3)]
+        splotch_get_geometry(self.ws.data_ptr(), self.ws_bytes, *[o.data_ptr() if self.dp.n else None for o in out],
+                             self.stream_ptr())
+        return out
+
+    def order(self):
+        t = self.torch
+        inf = self.info()
+        out = t.empty(max(inf.visible, 1), dtype=t.int32, device=self.device)
+        splotch_get_order(self.ws.data_ptr(), self.ws_bytes, out.data_ptr(), self.stream_ptr())
+        return out[:inf.visible]
+
+    def tile_lists(self):
+        t = self.torch
+        inf = self.info()
+        offs = t.empty(inf.ntiles + 1, dtype=t.int32, device=self.device)
+        lst = t.empty(max(inf.tile_entries, 1), dtype=t.int32, device=self.device)
+        splotch_get_tile_lists(self.ws.data_ptr(), self.ws_bytes, offs.data_ptr(), lst.data_ptr(),
+                               max(inf.tile_entries, 1), self.stream_ptr())
+        return offs, lst[:inf.tile_entries]
+
+    def fragments(self) -> int:
+        """F: (pixel, particle) pairs of the last transform that pass the membership test."""
+        t = self.torch
+        out = t.zeros(1, dtype=t.int64, device=self.device)
+        splotch_count_fragments(self.params, self.cam, self.dp.n, self.ws.data_ptr(), self.ws_bytes, out.data_ptr(),
+                                self.stream_ptr())
+        return int(out.item())
+
+    def colors(self):
+        t = self.torch
+        out = t.empty((max(self.dp.n, 1), 4), dtype=t.float32, device=self.device)
+        splotch_get_colors(self.ws.data_ptr(), self.ws_bytes, out.data_ptr(), self.stream_ptr())
+        return out[:self.dp.n]

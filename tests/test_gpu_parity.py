@@ -1,0 +1,139 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bit-exact: depth keys, boxes, screen positions and radii (the C12 geometry
+spec), the render order and the per-tile lists.  Images: max-abs error per
+RGB channel within 1e-4 of that channel's oracle maximum."""
+import numpy as np
+import pytest
+
+import synth
+from tests._common import TOL, gpu_render, image_error, oracle_render, small_two_species
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1004_1302_gb300 import splotch as S
+    S.build()
+    S.load()
+
+
+def _compare_frame(g, o, *, lists=True, image=True):
+    np.testing.assert_array_equal(g.key, o.geo.key)
+    np.testing.assert_array_equal(g.box, o.geo.bbox)
+    np.testing.assert_array_equal(g.sx.view(np.uint32), o.geo.sx.view(np.uint32))
+    np.testing.assert_array_equal(g.sy.view(np.uint32), o.geo.sy.view(np.uint32))
+    np.testing.assert_array_equal(g.r2.view(np.uint32), o.geo.r2.view(np.uint32))
+    assert g.info.visible == o.order.size
+    np.testing.assert_array_equal(g.order, o.order)
+    assert g.info.tile_entries == o.tile_list.size
+    if lists:
+        np.testing.assert_array_equal(g.offsets.astype(np.uint64), o.offsets)
+        np.testing.assert_array_equal(g.tile_list, o.tile_list)
+    vis = o.geo.visible
+    # colour: E and A per particle (float vs double)
+    np.testing.assert_allclose(g.colors[:, :3], o.E, rtol=3e-6, atol=1e-7)
+    np.testing.assert_allclose(g.colors[:, 3], o.A[:, 0], rtol=0, atol=0)
+    if image:
+        err = image_error(g.image, o.image)
+        assert (err <= TOL).all(), f"image error per channel {err}"
+    return vis
+
+
+def test_config0_emission_full_size():
+    ps, cam = synth.config0()
+    pal = synth.colormap()
+    g = gpu_render(ps, cam, pal, 0)
+    o = oracle_render(ps, cam, pal, 0)
+    _compare_frame(g, o)
+    assert g.info.status == 0 and g.info.visible == 100_000
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_two_species_ragged(mode, tile):
+    ps, cam = small_two_species(60_000, 330, 190)
+    pal = synth.colormap()
+    g = gpu_render(ps, cam, pal, mode, tile=tile)
+    o = oracle_render(ps, cam, pal, mode, tile=tile)
+    _compare_frame(g, o)
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_reduced_precision_intensity(dtype):
+    ps, cam = small_two_species(80_000, 320, 180)
+    pal = synth.colormap()
+    g = gpu_render(ps, cam, pal, 1, dtype=dtype)
+    o = oracle_render(ps, cam, pal, 1, dtype=dtype)        # same rounded inputs: compute error
+    _compare_frame(g, o)
+    full = oracle_render(ps, cam, pal, 1, dtype="f32")      # unrounded inputs: representation error (reported)
+    rep = image_error(g.image, full.image)
+    print(f"{dtype}: representation error per channel {rep}")
+    assert (rep < 0.05).all()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_threshold_and_batch_do_not_change_the_image(mode):
+    ps, cam = small_two_species(50_000, 256, 160)
+    pal = synth.colormap()
+    ref = gpu_render(ps, cam, pal, mode, batch=128)
+    for kw in (dict(large_threshold_px=1), dict(large_threshold_px=10**8), dict(batch=64), dict(batch=256)):
+        g = gpu_render(ps, cam, pal, mode, **kw)
+        np.testing.assert_array_equal(g.tile_list, ref.tile_list)
+        np.testing.assert_array_equal(g.image, ref.image)
+    assert gpu_render(ps, cam, pal, mode, large_threshold_px=1).info.large == ref.info.visible
+
+
+def test_capacity_overflow_is_reported_and_recovered():
+    ps, cam = small_two_species(30_000, 200, 120)
+    pal = synth.colormap()
+    ref = gpu_render(ps, cam, pal, 1)
+    g = gpu_render(ps, cam, pal, 1, max_tile_entries=1000)   # grows after the device reports the overflow
+    np.testing.assert_array_equal(g.image, ref.image)
+
+
+def _ps(x, y, z, h, v, sp):
+    return synth.ParticleSet(*[np.asarray(a, np.float32) for a in (x, y, z, h, v)], sp)
+
+
+def test_edge_cases():
+    pal = synth.colormap()
+    cam = synth.CameraSpec((0.5, 0.5, -1.5), (0.5, 0.5, 0.5), (0, 1, 0), 45.0, 97, 61)
+    sp = [synth.Species(0, 0, use_log=1, brightness=1.0, absorption=0.3)]
+    # no particles
+    g = gpu_render(_ps([], [], [], [], [], sp), cam, pal, 1)
+    assert g.image.shape == (61, 97, 3) and g.image.max() == 0 and g.info.visible == 0
+    # all culled: behind the camera, off screen
+    sp2 = [synth.Species(0, 2, use_log=1, brightness=1.0, absorption=0.3)]
+    g = gpu_render(_ps([0.5, 9.0], [0.5, 0.5], [-3.0, 0.5], [0.01, 0.01], [1, 2], sp2), cam, pal, 1)
+    assert g.image.max() == 0 and g.info.visible == 0 and g.info.tile_entries == 0
+    # one particle covering the whole image (cooperative path), one on the border, one tiny
+    sp3 = [synth.Species(0, 3, use_log=1, brightness=0.7, absorption=0.4)]
+    ps = _ps([0.5, 0.5 + 0.41, 0.45], [0.5, 0.5, 0.52], [0.5, 0.5, 0.1], [0.5, 0.05, 1e-5], [1.0, 3.0, 2.0], sp3)
+    for mode in (0, 1, 2):
+        g = gpu_render(ps, cam, pal, mode, tile=8)
+        o = oracle_render(ps, cam, pal, mode, tile=8)
+        _compare_frame(g, o)
+        assert g.info.large >= 1
+
+
+@pytest.mark.slow
+def test_config1_full_size_lists_and_sampled_pixels():
+    """10M particles, 1920x1080, absorptive, the launch configuration of the
+    benchmark: keys, order and tile lists bit-exact; sampled pixels (random,
+    three whole rows, and the brightest GPU pixels) within tolerance."""
+    ps, cam = synth.config1()
+    pal = synth.colormap()
+    g = gpu_render(ps, cam, pal, 1, tile=16, batch=128)
+    rng = np.random.default_rng(7)
+    pix = np.stack([rng.integers(0, 1920, 20000), rng.integers(0, 1080, 20000)], axis=1)
+    rows = [np.stack([np.arange(1920), np.full(1920, r)], axis=1) for r in (0, 540, 1079)]
+    hot = [np.array(np.unravel_index(np.argmax(g.image[:, :, c]), (1080, 1920))[::-1])[None] for c in range(3)]
+    pix = np.concatenate([pix, *rows, *hot]).astype(np.int32)
+    o = oracle_render(ps, cam, pal, 1, tile=16, pixels=pix)
+    _compare_frame(g, o, image=False)
+    got = g.image[pix[:, 1], pix[:, 0]].astype(np.float64)
+    err = np.abs(got - o.image).max(axis=0) / np.abs(o.image).max(axis=0)
+    assert (err <= TOL).all(), err
+    assert g.info.large > 0
