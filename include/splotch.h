@@ -236,6 +236,33 @@ int splotch_count_fragments(const splotch_render_params *params, const splotch_c
                             void *workspace, size_t workspace_bytes, uint64_t *out, void *stream);
 uint64_t splotch_launch_count(void);
 
+/*
+ * Depth sort without any device allocation, for callers that cannot call
+ * cudaMalloc while they run (for example a renderer embedded in a host
+ * application that owns all device memory through its own fixed pool, or a
+ * real-time loop where an allocation, which can synchronise the device, is
+ * not allowed after start-up).  The paper has no counterpart: it is a
+ * deployment convenience of this library.
+ *
+ * key: device, n depth keys as splotch_transform writes them (0xFFFFFFFF for
+ * a culled particle).  order: device, room for n uint32; receives the
+ * indices of the non-culled keys in ascending key order, ties by ascending
+ * index (the order splotch_sort gives).  count: device, one uint32, receives
+ * how many indices were written.  The caller owns all three buffers.
+ *
+ * The sort's scratch is a fixed array inside the library (about 4.3 MB on
+ * every GPU that loads it, held until the process exits); no call allocates
+ * or frees memory.  n above SPLOTCH_NO_ALLOC_MAX_KEYS returns SPLOTCH_ERR_ARG
+ * without enqueuing anything.  The first call on a device looks up the
+ * array's device address (with that device current); make that first call
+ * before capturing a stream.  All calls share the one array and it keeps the
+ * last call's contents, so calls whose work overlaps on the GPU (different
+ * streams, or different host threads on one device) race and must be
+ * serialised by the caller.  Asynchronous on `stream` like the other calls.
+ */
+#define SPLOTCH_NO_ALLOC_MAX_KEYS (1u << 18)
+int splotch_sort_keys_no_alloc(const uint32_t *key, uint32_t n, uint32_t *order, uint32_t *count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

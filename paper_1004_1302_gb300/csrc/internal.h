@@ -138,6 +138,7 @@ cudaError_t launch_transform(const TransformArgs &a, void *ws, const Layout &L, 
 cudaError_t launch_colorize(const ColorizeArgs &a, void *ws, const Layout &L, cudaStream_t st);
 cudaError_t launch_sort(void *ws, const Layout &L, int mode, cudaStream_t st);
 cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st);
+cudaError_t launch_sort_finish(Header *hdr, cudaStream_t st);   // absorptive ordering of a depth sort
 cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStream_t st);
 cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float *image, cudaStream_t st);
 cudaError_t launch_count_fragments(void *ws, const Layout &L, uint64_t *out, cudaStream_t st);

@@ -196,6 +196,12 @@ __global__ void k_sort_finish(Header *hdr, int absorptive) {
     hdr->sorted_buf = (passes - 1) & 1u;
 }
 
+cudaError_t launch_sort_finish(Header *hdr, cudaStream_t st) {
+    k_sort_finish<<<1, 32, 0, st>>>(hdr, 1);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sort(void *ws, const Layout &L, int mode, cudaStream_t st) {
     Header *hdr = header(ws);
     const bool absorptive = mode == SPLOTCH_ABSORPTIVE;

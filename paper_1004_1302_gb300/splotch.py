@@ -19,7 +19,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "_splotch.so")
-SOURCES = ["splotch_api.cu", "transform.cu", "sort.cu", "bin.cu", "render.cu"]
+SOURCES = ["splotch_api.cu", "transform.cu", "sort.cu", "bin.cu", "render.cu", "no_alloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 OK, ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_TIMEOUT, ERR_OOM_ADMISSION, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
@@ -112,7 +112,7 @@ EXPORTS = ["splotch_abi_version", "splotch_status_string", "splotch_camera_init"
            "splotch_transform", "splotch_colorize", "splotch_render", "splotch_sort", "splotch_bin",
            "splotch_render_tiles", "splotch_frame_info", "splotch_get_keys", "splotch_get_geometry",
            "splotch_get_order", "splotch_get_tile_lists", "splotch_get_colors", "splotch_count_fragments",
-           "splotch_launch_count"]
+           "splotch_launch_count", "splotch_sort_keys_no_alloc"]
 
 _lib = None
 
@@ -146,6 +146,7 @@ def load(path: str | None = None):
         "splotch_get_colors": ([V, ctypes.c_size_t, V, V], I32),
         "splotch_count_fragments": ([P(RenderParams), P(Camera), U64, V, ctypes.c_size_t, V, V], I32),
         "splotch_launch_count": ([], U64),
+        "splotch_sort_keys_no_alloc": ([V, ctypes.c_uint32, V, V, V], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -240,6 +241,15 @@ def splotch_get_colors(ws, ws_bytes, ea, stream):
 def splotch_count_fragments(params, cam, n, ws, ws_bytes, out, stream):
     _check(load().splotch_count_fragments(ctypes.byref(params), ctypes.byref(cam), n, ws, ws_bytes, out, stream),
            "splotch_count_fragments")
+
+
+NO_ALLOC_MAX_KEYS = 1 << 18
+
+
+def splotch_sort_keys_no_alloc(key: int, n: int, order: int, count: int, stream: int):
+    """Depth sort whose scratch is a fixed array inside the library (no
+    device allocation; see include/splotch.h)."""
+    _check(load().splotch_sort_keys_no_alloc(key, n, order, count, stream), "splotch_sort_keys_no_alloc")
 
 
 def splotch_launch_count() -> int:
