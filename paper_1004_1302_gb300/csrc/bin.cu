@@ -2,7 +2,7 @@
 // entry (tile id, particle) per tile its box meets.  Entry offsets come from
 // an exclusive scan of the per-particle tile counts, so the entries of one
 // particle sit at fixed positions whatever the thread that writes them.
-// Particles touching more tiles than a threshold are written by a whole CTA
+// Particles touching more tiles than a threshold are split over a whole CTA
 // (the "split particles" idea of Section 3.2 applied to the emission of
 // work items).  A stable radix sort by tile id then yields per-tile lists in
 // render order, and a boundary pass turns the sorted ids into tile offsets.
@@ -11,15 +11,17 @@
 
 namespace spl {
 
-__device__ __forceinline__ uint32_t tiles_of(const ushort4 b, int T) {
-    return (uint32_t)(b.z / T - b.x / T + 1) * (uint32_t)(b.w / T - b.y / T + 1);
+constexpr int kBinStep = 2048;   // particles per CTA step of the emission kernel
+
+__device__ __forceinline__ uint32_t tiles_of(const ushort4 b, int tshift) {
+    return (uint32_t)((b.z >> tshift) - (b.x >> tshift) + 1) * (uint32_t)((b.w >> tshift) - (b.y >> tshift) + 1);
 }
 
 __device__ __forceinline__ void bin_range(uint32_t ctas, uint32_t n, uint64_t *beg, uint64_t *end) {
-    const uint64_t tiles = (n + (uint64_t)kSortTile - 1) / kSortTile;
-    const uint64_t tpc = (tiles + ctas - 1) / ctas;
-    *beg = (uint64_t)blockIdx.x * tpc * kSortTile;
-    uint64_t e = *beg + tpc * kSortTile;
+    const uint64_t steps = (n + (uint64_t)kBinStep - 1) / kBinStep;
+    const uint64_t spc = (steps + ctas - 1) / ctas;
+    *beg = (uint64_t)blockIdx.x * spc * kBinStep;
+    uint64_t e = *beg + spc * kBinStep;
     *end = e < n ? e : n;
     if (*beg > *end) *beg = *end;
 }
@@ -31,7 +33,7 @@ __global__ void __launch_bounds__(256) k_bin_reduce(BinArgs a) {
     uint64_t beg, end;
     bin_range(a.ctas, n, &beg, &end);
     unsigned long long sum = 0;
-    for (uint64_t k = beg + threadIdx.x; k < end; k += blockDim.x) sum += tiles_of(a.box[list[k]], a.tile);
+    for (uint64_t k = beg + threadIdx.x; k < end; k += blockDim.x) sum += tiles_of(a.box[list[k]], a.tshift);
     unsigned long long tot;
     block_exclusive_scan64<256>(sum, ws, &tot);
     if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
@@ -62,78 +64,111 @@ __global__ void __launch_bounds__(1024) k_bin_scan(BinArgs a) {
     }
 }
 
-// Each CTA walks its range in 4096-item steps; thread t owns items
-// 16t..16t+15 of a step so that a block scan gives offsets in list order.
+// Each CTA walks its range in steps of kBinStep particles (list order).
+// A particle touching at most `large_tiles` tiles is written by the thread
+// that owns it; the step's larger particles are split over the CTA's warps,
+// one warp per particle with its lanes across a row of tiles, so the writes
+// of a row are contiguous.
 __global__ void __launch_bounds__(256) k_bin_emit(BinArgs a) {
-    __shared__ unsigned long long ws[9];
+    constexpr int kPer = kBinStep / 256;
+    __shared__ uint32_t s_p[kBinStep];        // particle index per item
+    __shared__ uint32_t s_off[kBinStep];      // tiles per item, then its entry offset within the step
+    __shared__ uint32_t s_lidx[kBinStep];     // items of the large particles, in list order
+    __shared__ ushort4 s_box[kBinStep];       // tile box per item: tx0, ty0, tx1, ty1
+    __shared__ uint32_t ws32[9];
     const uint32_t n = a.hdr->visible;
     const uint32_t *list = a.hdr->sorted_buf ? a.list[1] : a.list[0];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t beg, end;
     bin_range(a.ctas, n, &beg, &end);
     unsigned long long running = a.part[blockIdx.x];
-    constexpr int kPer = kSortTile / 256;
-    for (uint64_t step = beg; step < end; step += kSortTile) {
-        uint32_t p[kPer], nt[kPer];
-        unsigned long long mine = 0;
+    uint32_t nlarge_cta = 0;
+    for (uint64_t step = beg; step < end; step += kBinStep) {
+        const uint32_t m = (uint32_t)min((uint64_t)kBinStep, end - step);
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
-            const uint64_t k = step + threadIdx.x * kPer + q;
-            p[q] = k < end ? list[k] : 0u;
-            nt[q] = k < end ? tiles_of(a.box[p[q]], a.tile) : 0u;
-            mine += nt[q];
-        }
-        unsigned long long tot;
-        unsigned long long off = running + block_exclusive_scan64<256>(mine, ws, &tot);
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            if (nt[q] > a.large_tiles) {
-                const uint32_t slot = atomicAdd(&a.hdr->n_large, 1u);
-                a.large[slot] = make_uint2((uint32_t)(off < a.cap ? off : a.cap), p[q]);
-            } else if (nt[q]) {
-                const ushort4 b = a.box[p[q]];
-                const int tx0 = b.x / a.tile, tx1 = b.z / a.tile, ty0 = b.y / a.tile, ty1 = b.w / a.tile;
-                unsigned long long e = off;
-                for (int ty = ty0; ty <= ty1; ++ty)
-                    for (int tx = tx0; tx <= tx1; ++tx, ++e)
-                        if (e < a.cap) {
-                            a.ek[e] = (uint32_t)(ty * a.ntx + tx);
-                            a.ev[e] = p[q];
-                        }
+            const uint32_t j = threadIdx.x + 256u * q;
+            uint32_t p = 0, nt = 0;
+            ushort4 tb = make_ushort4(1, 1, 0, 0);
+            if (j < m) {
+                p = list[step + j];
+                const ushort4 b = a.box[p];
+                tb = make_ushort4(b.x >> a.tshift, b.y >> a.tshift, b.z >> a.tshift, b.w >> a.tshift);
+                nt = (uint32_t)(tb.z - tb.x + 1) * (uint32_t)(tb.w - tb.y + 1);
             }
+            s_p[j] = p;
+            s_off[j] = nt;
+            s_box[j] = tb;
+        }
+        __syncthreads();
+        // blocked arrangement: thread t owns items kPer*t .. kPer*t + kPer - 1
+        uint32_t nt[kPer];
+        uint32_t mine = 0, mine_large = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            nt[q] = s_off[kPer * threadIdx.x + q];
+            mine += nt[q];
+            mine_large += nt[q] > a.large_tiles;
+        }
+        uint32_t tot, ltot;
+        uint32_t off = block_exclusive_scan<256>(mine, ws32, &tot);
+        uint32_t lpos = block_exclusive_scan<256>(mine_large, ws32, &ltot);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t j = kPer * threadIdx.x + q;
+            s_off[j] = off;
+            if (nt[q] > a.large_tiles) s_lidx[lpos++] = j;
             off += nt[q];
         }
-        running += tot;
-    }
-}
-
-// Cooperative emission of the large particles: one CTA per particle.
-__global__ void __launch_bounds__(256) k_emit_large(BinArgs a) {
-    const uint32_t nl = a.hdr->n_large;
-    for (uint32_t L = blockIdx.x; L < nl; L += gridDim.x) {
-        const uint2 item = a.large[L];
-        const ushort4 b = a.box[item.y];
-        const int tx0 = b.x / a.tile, ty0 = b.y / a.tile;
-        const uint32_t w = (uint32_t)(b.z / a.tile - tx0 + 1), h = (uint32_t)(b.w / a.tile - ty0 + 1);
-        const uint32_t nt = w * h;
-        for (uint32_t j = threadIdx.x; j < nt; j += blockDim.x) {
-            const unsigned long long e = (unsigned long long)item.x + j;
-            if (e < a.cap) {
-                a.ek[e] = (uint32_t)((ty0 + (int)(j / w)) * a.ntx + tx0 + (int)(j % w));
-                a.ev[e] = item.y;
-            }
+        __syncthreads();
+        // small particles: the owner writes its entries
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t j = kPer * threadIdx.x + q;
+            if (nt[q] == 0 || nt[q] > a.large_tiles) continue;
+            const uint32_t p = s_p[j];
+            const ushort4 b = s_box[j];
+            unsigned long long e = running + s_off[j];
+            for (int ty = b.y; ty <= b.w; ++ty)
+                for (int tx = b.x; tx <= b.z; ++tx, ++e)
+                    if (e < a.cap) {
+                        a.ek[e] = (uint32_t)(ty * a.ntx + tx);
+                        a.ev[e] = p;
+                    }
         }
+        // large particles: one warp per particle, lanes across a row of tiles
+        for (uint32_t i = warp; i < ltot; i += 8) {
+            const uint32_t j = s_lidx[i];
+            const uint32_t p = s_p[j];
+            const ushort4 b = s_box[j];
+            const uint32_t w = (uint32_t)(b.z - b.x + 1);
+            unsigned long long e0 = running + s_off[j];
+            for (int ty = b.y; ty <= b.w; ++ty, e0 += w)
+                for (uint32_t c = lane; c < w; c += 32) {
+                    const unsigned long long e = e0 + c;
+                    if (e < a.cap) {
+                        a.ek[e] = (uint32_t)(ty * a.ntx + b.x) + c;
+                        a.ev[e] = p;
+                    }
+                }
+        }
+        nlarge_cta += ltot;
+        running += tot;
+        __syncthreads();
     }
+    if (threadIdx.x == 0 && nlarge_cta) atomicAdd(&a.hdr->n_large, nlarge_cta);
 }
 
 // Tile offsets from tile-sorted entry ids: offsets[t] = first entry of tile t.
 __global__ void __launch_bounds__(256) k_tile_offsets(const Header *hdr, const uint32_t *ek, uint32_t *toff,
                                                       uint32_t ntiles) {
     const uint32_t D = hdr->tile_entries32;
+    const uint32_t stride = gridDim.x * blockDim.x;
     if (D == 0) {
-        for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += gridDim.x * blockDim.x) toff[t] = 0;
+        for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += stride) toff[t] = 0;
         return;
     }
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < D; e += gridDim.x * blockDim.x) {
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < D; e += stride) {
         const uint32_t t = ek[e];
         const uint32_t prev = e ? ek[e - 1] + 1u : 0u;
         for (uint32_t tt = prev; tt <= t; ++tt) toff[tt] = e;
@@ -160,17 +195,15 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     a.ctas = L.sort_ctas;
     a.ek = at<uint32_t>(ws, L.off_ek[0]);
     a.ev = at<uint32_t>(ws, L.off_ev[0]);
-    a.large = at<uint2>(ws, L.off_large);
     a.cap = L.cap;
     a.tile = L.tile;
     a.ntx = L.ntx;
     a.large_tiles = large_tiles;
+    a.tshift = L.tile == 8 ? 3 : (L.tile == 16 ? 4 : 5);
     k_bin_reduce<<<a.ctas, 256, 0, st>>>(a);
     k_bin_scan<<<1, 1024, 0, st>>>(a);
     k_bin_emit<<<a.ctas, 256, 0, st>>>(a);
-    const int sms = sm_count_bin();
-    k_emit_large<<<sms * 4, 256, 0, st>>>(a);
-    count_launches(4);
+    count_launches(3);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // Stable sort of the entries by tile id (only the bits a tile id can use).
@@ -196,8 +229,9 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
         e = launch_radix_pass(p, st);
         if (e != cudaSuccess) return e;
     }
-    k_tile_offsets<<<sms * 4, 256, 0, st>>>(hdr, at<uint32_t>(ws, L.off_ek[passes & 1]), at<uint32_t>(ws, L.off_toff),
-                                             L.ntiles);
+    const int sms = sm_count_bin();
+    k_tile_offsets<<<sms * 32, 256, 0, st>>>(hdr, at<uint32_t>(ws, L.off_ek[passes & 1]), at<uint32_t>(ws, L.off_toff),
+                                              L.ntiles);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -31,9 +31,9 @@ struct Layout {
     uint32_t ent_ctas;       // CTAs of a radix pass over tile entries
     uint32_t hist_ctas;      // max(sort_ctas, ent_ctas): rows of the histogram table
     uint32_t pad0;
-    uint64_t off_geo, off_col, off_key, off_box;
+    uint64_t off_geo, off_col, off_key, off_box;   // geo: {sx, sy, r2, -log2(e)/sigma_pix^2}; col: {Er, Eg, Eb, A}
     uint64_t off_sk[2], off_sv[2];
-    uint64_t off_large, off_part;
+    uint64_t off_part;
     uint64_t off_hist, off_htot;
     uint64_t off_toff;
     uint64_t off_ek[2], off_ev[2];
@@ -105,9 +105,8 @@ struct BinArgs {
     uint64_t *part;            // per-CTA partial sums
     uint32_t ctas;
     uint32_t *ek, *ev;         // emitted entries (tile id, particle)
-    uint2 *large;              // (entry offset, particle) of large particles
     uint64_t cap;
-    int tile, ntx;
+    int tile, ntx, tshift;     // tshift = log2(tile)
     uint32_t large_tiles;      // particles touching more tiles than this go to the cooperative path
 };
 

@@ -1,13 +1,13 @@
 // Tile renderer: one CTA per screen tile, two horizontally adjacent pixels
 // per thread.  The tile's particle list is staged in batches into shared
-// memory (double-buffered asynchronous copies); each warp culls a batch
-// against its 16x4 (or 8x8) pixel block with one test per lane and a ballot,
+// memory (prefetched into registers one batch ahead); each warp culls a
+// batch against its 8x8 pixel block with one test per lane and a ballot,
 // then walks the surviving particles in list order.  Per pixel it evaluates
 // the truncated Gaussian footprint (Section 2, first item) and integrates
 // Eq. 1 (Section 2) across the particle layer:
 //   emission    C += E g
 //   absorptive  C += T_acc S, T_acc *= T, with T = exp(-A g),
-//               S = E (1 - T)/A = E g q(A g), q(y) = (1 - e^-y)/y
+//               S = E (1 - T)/A (E g when A = 0)
 //   E = A       C += E g, then I = 1 - exp(-C)
 // Packed f32x2 arithmetic does both pixels of a thread in one instruction.
 #include "internal.h"
@@ -32,27 +32,35 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
-// (1 - e^-y)/y = sum_k (-y)^k / (k+1)!, truncated after y^6: relative error
-// below y^7/8! (under 2e-7 for y <= 0.5).
-__device__ __forceinline__ float2 q_series(float2 y) {
-    float2 q = f2(1.0f / 5040.0f);
-    q = __ffma2_rn(q, y, f2(-1.0f / 720.0f));
-    q = __ffma2_rn(q, y, f2(1.0f / 120.0f));
-    q = __ffma2_rn(q, y, f2(-1.0f / 24.0f));
-    q = __ffma2_rn(q, y, f2(1.0f / 6.0f));
-    q = __ffma2_rn(q, y, f2(-0.5f));
-    q = __ffma2_rn(q, y, f2(1.0f));
+// An absorbing layer with A <= kSeriesMaxA takes its source and
+// transmission from a series: with yn = -A g,
+//   q = (1 - e^{-y})/y = 1 + yn/2 + yn^2/6 + yn^3/24 + ...
+// truncated after yn^3 (relative error below y^4/5! < 2.1e-6 for y <= 1/8),
+// S = E g q and T = 1 + yn q, with no cancellation; A = 0 gives q = 1, T = 1.
+// Larger A takes T from exp2 and S = E (1 - T)/A.
+constexpr float kSeriesMaxA = 0.125f;
+
+__device__ __forceinline__ float2 q_series(float2 yn) {
+    float2 q = f2(1.0f / 24.0f);
+    q = __ffma2_rn(q, yn, f2(1.0f / 6.0f));
+    q = __ffma2_rn(q, yn, f2(0.5f));
+    q = __ffma2_rn(q, yn, f2(1.0f));
     return q;
 }
+
+// A staged particle is laid out as ready-made operand pairs for the packed
+// two-pixel arithmetic, in four arrays (conflict-free stores):
+// {-sx, -sx, -sy, -sy}, {k, k, -A, -A}, {Er, Er, Eg, Eg}, {Eb, Eb, r2, A}
+// with k = -log2(e)/sigma_pix^2.
 
 template <int T, int MODE, int B>
 __global__ void __launch_bounds__(T * T / 2) k_render(RenderArgs a) {
     constexpr int kThreads = T * T / 2;
-    constexpr int WX = T >= 16 ? 16 : 8;        // warp block width in pixels
-    constexpr int WY = 64 / WX;                 // warp block height
+    constexpr int WX = 8, WY = 8;               // pixel block of one warp (two pixels per lane)
     constexpr int kWarpCols = T / WX;
-    __shared__ __align__(16) float4 sgeo[2][B];
-    __shared__ __align__(16) float4 scol[2][B];
+    constexpr int kPer = (B + kThreads - 1) / kThreads;
+    __shared__ __align__(16) float4 s0[2][B], s1[2][B], s2[2][B], s3[2][B];
+    __shared__ __align__(16) float4 scull[2][B];   // sx, sy, r2 for the cull test
 
     const int tile = blockIdx.x;
     const int tx = tile % a.ntx, ty = tile / a.ntx;
@@ -60,7 +68,7 @@ __global__ void __launch_bounds__(T * T / 2) k_render(RenderArgs a) {
     const int wx0 = tx * T + (warp % kWarpCols) * WX, wy0 = ty * T + (warp / kWarpCols) * WY;
     const int px0 = wx0 + 2 * (lane % (WX / 2)), py = wy0 + lane / (WX / 2);
     const float2 cx = make_float2((float)px0 + 0.5f, (float)px0 + 1.5f);
-    const float cy = (float)py + 0.5f;
+    const float2 cy = f2((float)py + 0.5f);
     // pixel-centre box of this warp, for the cull test
     const float xa = (float)wx0 + 0.5f, xb = (float)(wx0 + WX) - 0.5f;
     const float ya = (float)wy0 + 0.5f, yb = (float)(wy0 + WY) - 0.5f;
@@ -70,29 +78,51 @@ __global__ void __launch_bounds__(T * T / 2) k_render(RenderArgs a) {
     const bool ok = a.hdr->status == SPLOTCH_OK;
     const uint32_t begin = ok ? a.toff[tile] : 0u, end = ok ? a.toff[tile + 1] : 0u;
 
-    auto stage = [&](int buf, uint32_t base) {
+    // A batch is loaded into registers one batch ahead and written to shared
+    // memory (as operand pairs) after the current batch has been composited.
+    float4 rg[kPer], rc[kPer];
+    auto load = [&](uint32_t base) {
         const uint32_t nb = min((uint32_t)B, end - base);
-        for (uint32_t j = threadIdx.x; j < nb; j += kThreads) {
-            const uint32_t p = a.list[base + j];
-            cp_async16(&sgeo[buf][j], &a.geo[p]);
-            cp_async16(&scol[buf][j], &a.col[p]);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t j = threadIdx.x + q * kThreads;
+            if (j < nb) {
+                const uint32_t p = __ldg(&a.list[base + j]);
+                rg[q] = __ldg(&a.geo[p]);
+                rc[q] = __ldg(&a.col[p]);
+            }
+        }
+    };
+    auto store = [&](int buf, uint32_t base) {
+        const uint32_t nb = min((uint32_t)B, end - base);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t j = threadIdx.x + q * kThreads;
+            if (j < nb) {
+                const float4 g = rg[q], c = rc[q];
+                s0[buf][j] = make_float4(-g.x, -g.x, -g.y, -g.y);
+                s1[buf][j] = make_float4(g.w, g.w, -c.w, -c.w);
+                s2[buf][j] = make_float4(c.x, c.x, c.y, c.y);
+                s3[buf][j] = make_float4(c.z, c.z, g.z, c.w);
+                scull[buf][j] = g;
+            }
         }
     };
 
-    if (begin < end) stage(0, begin);
-    cp_async_commit();
+    if (begin < end) {
+        load(begin);
+        store(0, begin);
+    }
     int buf = 0;
     for (uint32_t base = begin; base < end; base += B, buf ^= 1) {
         const uint32_t next = base + B;
-        if (next < end) stage(buf ^ 1, next);
-        cp_async_commit();
-        cp_async_wait<1>();
+        if (next < end) load(next);
         __syncthreads();
         const uint32_t nb = min((uint32_t)B, end - base);
         for (uint32_t c = 0; c < nb; c += 32) {
             bool keep = false;
             if (c + lane < nb) {
-                const float4 g = sgeo[buf][c + lane];
+                const float4 g = scull[buf][c + lane];
                 const float qx = fminf(fmaxf(g.x, xa), xb), qy = fminf(fmaxf(g.y, ya), yb);
                 const float ddx = g.x - qx, ddy = g.y - qy;
                 // conservative: a pixel that passes the exact test is never culled
@@ -102,39 +132,38 @@ __global__ void __launch_bounds__(T * T / 2) k_render(RenderArgs a) {
             while (mask) {
                 const int j = __ffs(mask) - 1;
                 mask &= mask - 1;
-                const float4 g = sgeo[buf][c + j];
-                const float4 e = scol[buf][c + j];
-                const float2 dx = __fadd2_rn(cx, f2(-g.x));
-                const float dy = __fadd_rn(cy, -g.y);
-                const float2 d2 = __ffma2_rn(f2(dy), f2(dy), __fmul2_rn(dx, dx));
-                const float2 arg = __fmul2_rn(d2, f2(g.w));
+                const float4 p0 = s0[buf][c + j], p1 = s1[buf][c + j];
+                const float4 p2 = s2[buf][c + j], p3 = s3[buf][c + j];
+                const float2 dx = __fadd2_rn(cx, make_float2(p0.x, p0.y));
+                const float2 dy = __fadd2_rn(cy, make_float2(p0.z, p0.w));
+                const float2 d2 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
+                const float2 arg = __fmul2_rn(d2, make_float2(p1.x, p1.y));
                 float2 w;
-                w.x = d2.x < g.z ? ex2_approx(arg.x) : 0.0f;
-                w.y = d2.y < g.z ? ex2_approx(arg.y) : 0.0f;
+                w.x = d2.x < p3.z ? ex2_approx(arg.x) : 0.0f;
+                w.y = d2.y < p3.z ? ex2_approx(arg.y) : 0.0f;
                 if (MODE == SPLOTCH_ABSORPTIVE) {
-                    const float2 y = __fmul2_rn(w, f2(e.w));
-                    float2 s, t;
-                    if (e.w <= 0.5f) {
-                        const float2 q = q_series(y);
-                        s = __fmul2_rn(w, q);
-                        t = __ffma2_rn(make_float2(-y.x, -y.y), q, f2(1.0f));
+                    float2 t;
+                    if (p3.w <= kSeriesMaxA) {
+                        const float2 yn = __fmul2_rn(w, make_float2(p1.z, p1.w));
+                        const float2 q = q_series(yn);
+                        t = __ffma2_rn(yn, q, f2(1.0f));
+                        w = __fmul2_rn(w, q);
                     } else {
-                        t.x = ex2_approx(-1.4426950408889634f * y.x);
-                        t.y = ex2_approx(-1.4426950408889634f * y.y);
-                        const float inva = 1.0f / e.w;
-                        s = __fmul2_rn(__fadd2_rn(f2(1.0f), make_float2(-t.x, -t.y)), f2(inva));
+                        const float2 yl = __fmul2_rn(w, f2(-1.4426950408889634f * p3.w));
+                        t = make_float2(ex2_approx(yl.x), ex2_approx(yl.y));
+                        w = __fmul2_rn(__fadd2_rn(f2(1.0f), make_float2(-t.x, -t.y)), f2(1.0f / p3.w));
                     }
-                    w = __fmul2_rn(tacc, s);
+                    w = __fmul2_rn(tacc, w);
                     tacc = __fmul2_rn(tacc, t);
                 }
-                cr = __ffma2_rn(w, f2(e.x), cr);
-                cg = __ffma2_rn(w, f2(e.y), cg);
-                cb = __ffma2_rn(w, f2(e.z), cb);
+                cr = __ffma2_rn(w, make_float2(p2.x, p2.y), cr);
+                cg = __ffma2_rn(w, make_float2(p2.z, p2.w), cg);
+                cb = __ffma2_rn(w, make_float2(p3.x, p3.y), cb);
             }
         }
         __syncthreads();
+        if (next < end) store(buf ^ 1, next);
     }
-    cp_async_wait<0>();
 
     if (MODE == SPLOTCH_E_EQ_A) {
         cr = make_float2(-expm1f(-cr.x), -expm1f(-cr.y));

@@ -28,13 +28,28 @@ __device__ __forceinline__ void cta_range(const RadixPass &P, uint32_t n, uint64
     if (*beg > *end) *beg = *end;
 }
 
+// Lanes of the warp whose 9-bit value equals this lane's (8 digit bits and
+// an "invalid" bit), from nine ballots.
+__device__ __forceinline__ uint32_t same_digit_lanes(uint32_t v) {
+    uint32_t m = 0xFFFFFFFFu;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        const uint32_t bit = (v >> b) & 1u;
+        const uint32_t x = __ballot_sync(0xFFFFFFFFu, bit);
+        m &= bit ? x : ~x;
+    }
+    return m;
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(RadixPass P) {
-    __shared__ uint32_t cnt[kRadix];
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) cnt[d] = 0;
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ uint32_t cnt[kWarps][kRadix];
+    for (int q = threadIdx.x; q < kWarps * kRadix; q += blockDim.x) (&cnt[0][0])[q] = 0;
     __syncthreads();
     if (pass_skipped(P)) return;
     const uint32_t n = item_count(P);
     const uint32_t kmin = P.depth_pass >= 0 ? P.hdr->key_min : 0u;
+    const uint32_t warp = threadIdx.x >> 5;
     uint64_t beg, end;
     cta_range(P, n, &beg, &end);
     for (uint64_t base = beg; base < end; base += 4 * kSortThreads) {
@@ -51,12 +66,21 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(RadixPass P) {
         for (int q = 0; q < 4; ++q) {
             uint32_t d = kRadix;
             if (i + q < end && !(P.skip_invalid && k[q] == kInvalidKey)) d = ((k[q] - kmin) >> P.shift) & P.mask;
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-            if (d < (uint32_t)kRadix && (peers & lanemask_lt()) == 0) atomicAdd(&cnt[d], __popc(peers));
+            const uint32_t d0 = __shfl_sync(0xFFFFFFFFu, d, 0);
+            if (__all_sync(0xFFFFFFFFu, d == d0)) {
+                if (lane_id() == 0 && d0 < (uint32_t)kRadix) cnt[warp][d0] += 32;
+            } else if (d < (uint32_t)kRadix) {
+                atomicAdd(&cnt[warp][d], 1u);
+            }
         }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) P.hist[(uint64_t)d * P.hist_stride + blockIdx.x] = cnt[d];
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) c += cnt[w][d];
+        P.hist[(uint64_t)d * P.hist_stride + blockIdx.x] = c;
+    }
 }
 
 // One block per digit: exclusive scan of that digit's per-CTA counts and the
@@ -85,85 +109,95 @@ __global__ void __launch_bounds__(1024) k_radix_scan(RadixPass P) {
     if (threadIdx.x == 0) P.htot[d] = total;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(RadixPass P) {
+// Scatter of one pass: each CTA ranks its 4096-item tiles in shared memory
+// (per-warp digit counters, ranks from ballots) and writes each digit's run
+// to its global position.
+constexpr int kDsThreads = 512;
+constexpr int kDsWarps = kDsThreads / 32;
+constexpr int kDsItems = kSortTile / kDsThreads;
+
+__global__ void __launch_bounds__(kDsThreads) k_radix_downsweep(RadixPass P) {
     __shared__ uint32_t skey[kSortTile];
     __shared__ uint32_t sval[kSortTile];
-    __shared__ uint32_t wcnt[kRadix][kSortThreads / 32];
+    __shared__ uint16_t wcnt[kDsWarps][kRadix];   // per-warp digit counters (digit-contiguous: no bank conflicts)
     __shared__ uint32_t base[kRadix];
     __shared__ uint32_t lstart[kRadix + 1];
     __shared__ uint32_t ltot[kRadix];
-    __shared__ uint32_t scratch[kSortThreads / 32 + 1];
-    constexpr int kWarps = kSortThreads / 32;
+    __shared__ uint32_t scratch[kDsWarps + 1];
     if (pass_skipped(P)) return;
     const uint32_t n = item_count(P);
     const uint32_t kmin = P.depth_pass >= 0 ? P.hdr->key_min : 0u;
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    const bool owns_digit = threadIdx.x < (uint32_t)kRadix;
     uint64_t beg, end;
     cta_range(P, n, &beg, &end);
     {
-        const uint32_t d = threadIdx.x;  // kSortThreads == kRadix
         uint32_t tot;
-        uint32_t pre = block_exclusive_scan<kSortThreads>(P.htot[d], scratch, &tot);
-        base[d] = pre + P.hist[(uint64_t)d * P.hist_stride + blockIdx.x];
+        const uint32_t pre = block_exclusive_scan<kDsThreads>(owns_digit ? P.htot[threadIdx.x] : 0u, scratch, &tot);
+        if (owns_digit) base[threadIdx.x] = pre + P.hist[(uint64_t)threadIdx.x * P.hist_stride + blockIdx.x];
     }
     __syncthreads();
     const uint32_t lt = lanemask_lt();
     for (uint64_t tile = beg; tile < end; tile += kSortTile) {
-        for (int q = threadIdx.x; q < kRadix * kWarps; q += kSortThreads) (&wcnt[0][0])[q] = 0;
+        for (int q = threadIdx.x; q < kRadix * kDsWarps / 2; q += kDsThreads)
+            reinterpret_cast<uint32_t *>(&wcnt[0][0])[q] = 0;
         __syncthreads();
-        uint32_t key[kSortItems], val[kSortItems], dig[kSortItems], rnk[kSortItems];
-        const uint64_t wbase = tile + (uint64_t)warp * (kSortItems * 32);
+        uint32_t key[kDsItems], val[kDsItems], dr[kDsItems];   // dr = rank << 9 | digit
+        const uint64_t wbase = tile + (uint64_t)warp * (kDsItems * 32);
 #pragma unroll
-        for (int r = 0; r < kSortItems; ++r) {
+        for (int r = 0; r < kDsItems; ++r) {
             const uint64_t i = wbase + r * 32 + lane;
             key[r] = i < end ? P.key_in[i] : kInvalidKey;
             val[r] = i < end ? (P.val_in ? P.val_in[i] : (uint32_t)i) : 0u;
         }
 #pragma unroll
-        for (int r = 0; r < kSortItems; ++r) {
+        for (int r = 0; r < kDsItems; ++r) {
             const uint64_t i = wbase + r * 32 + lane;
             uint32_t d = kRadix;
             if (i < end && !(P.skip_invalid && key[r] == kInvalidKey)) d = ((key[r] - kmin) >> P.shift) & P.mask;
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            const uint32_t peers = same_digit_lanes(d);
             uint32_t c = 0;
-            if (d < (uint32_t)kRadix) c = wcnt[d][warp];
+            if (d < (uint32_t)kRadix) c = wcnt[warp][d];
             __syncwarp();
-            if (d < (uint32_t)kRadix && (peers & lt) == 0) wcnt[d][warp] = c + __popc(peers);
+            if (d < (uint32_t)kRadix && (peers & lt) == 0) wcnt[warp][d] = (uint16_t)(c + __popc(peers));
             __syncwarp();
-            dig[r] = d;
-            rnk[r] = c + __popc(peers & lt);
+            dr[r] = ((c + __popc(peers & lt)) << 9) | d;
         }
         __syncthreads();
         {
-            const uint32_t d = threadIdx.x;
             uint32_t s = 0;
+            if (owns_digit) {
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) s += wcnt[d][w];
-            ltot[d] = s;
-            uint32_t tot;
-            uint32_t pre = block_exclusive_scan<kSortThreads>(s, scratch, &tot);
-            lstart[d] = pre;
-            if (d == 0) lstart[kRadix] = tot;
-            uint32_t run = pre;
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                const uint32_t c = wcnt[d][w];
-                wcnt[d][w] = run;
-                run += c;
+                for (int w = 0; w < kDsWarps; ++w) s += wcnt[w][threadIdx.x];
+                ltot[threadIdx.x] = s;
             }
+            uint32_t tot;
+            const uint32_t pre = block_exclusive_scan<kDsThreads>(s, scratch, &tot);
+            if (owns_digit) {
+                lstart[threadIdx.x] = pre;
+                uint32_t run = pre;
+#pragma unroll
+                for (int w = 0; w < kDsWarps; ++w) {
+                    const uint32_t c = wcnt[w][threadIdx.x];
+                    wcnt[w][threadIdx.x] = (uint16_t)run;
+                    run += c;
+                }
+            }
+            if (threadIdx.x == 0) lstart[kRadix] = tot;
         }
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < kSortItems; ++r) {
-            if (dig[r] < (uint32_t)kRadix) {
-                const uint32_t pos = wcnt[dig[r]][warp] + rnk[r];
+        for (int r = 0; r < kDsItems; ++r) {
+            const uint32_t d = dr[r] & 511u;
+            if (d < (uint32_t)kRadix) {
+                const uint32_t pos = wcnt[warp][d] + (dr[r] >> 9);
                 skey[pos] = key[r];
                 sval[pos] = val[r];
             }
         }
         __syncthreads();
         const uint32_t nvalid = lstart[kRadix];
-        for (uint32_t j = threadIdx.x; j < nvalid; j += kSortThreads) {
+        for (uint32_t j = threadIdx.x; j < nvalid; j += kDsThreads) {
             const uint32_t k = skey[j];
             const uint32_t d = ((k - kmin) >> P.shift) & P.mask;
             const uint32_t pos = base[d] + (j - lstart[d]);
@@ -171,7 +205,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(RadixPass P) {
             P.val_out[pos] = sval[j];
         }
         __syncthreads();
-        base[threadIdx.x] += ltot[threadIdx.x];
+        if (owns_digit) base[threadIdx.x] += ltot[threadIdx.x];
         __syncthreads();
     }
 }
@@ -179,7 +213,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(RadixPass P) {
 cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st) {
     k_radix_upsweep<<<p.ctas, kSortThreads, 0, st>>>(p);
     k_radix_scan<<<kRadix, 1024, 0, st>>>(p);
-    k_radix_downsweep<<<p.ctas, kSortThreads, 0, st>>>(p);
+    k_radix_downsweep<<<p.ctas, kDsThreads, 0, st>>>(p);
     count_launches(3);
     return cudaGetLastError();
 }

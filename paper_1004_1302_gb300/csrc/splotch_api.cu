@@ -51,7 +51,6 @@ int compute_layout(uint64_t n, int width, int height, int tile, uint64_t cap, La
         L.off_sk[b] = take(n * 4);
         L.off_sv[b] = take(n * 4);
     }
-    L.off_large = take(n * 8);
     L.off_part = take((uint64_t)kMaxSortCtas * 8);
     L.off_hist = take((uint64_t)kRadix * L.hist_ctas * 4);
     L.off_htot = take((uint64_t)kRadix * 4);
@@ -65,8 +64,8 @@ int compute_layout(uint64_t n, int width, int height, int tile, uint64_t cap, La
     return SPLOTCH_OK;
 }
 
-// Particle-count-only offsets (geometry and colour records come first and do
-// not depend on the image or the tile-entry capacity).
+// The per-particle records come first, so their offsets depend on the
+// particle count alone (not on the image or the tile-entry capacity).
 static uint64_t col_offset(uint64_t n) { return align256(kHeaderBytes + n * 16); }
 
 static int check_ws(const void *ws, size_t bytes, const Layout &L) {
@@ -379,8 +378,8 @@ int splotch_get_colors(const void *workspace, size_t workspace_bytes, float *ea,
     int s = read_header(workspace, workspace_bytes, st, &h);
     if (s) return s;
     if (!ea) return SPLOTCH_ERR_ARG;
-    if (h.layout.n && cudaMemcpyAsync(ea, at<float>(const_cast<void *>(workspace), h.layout.off_col),
-                                      h.layout.n * 16, cudaMemcpyDeviceToDevice, st))
+    if (h.layout.n && cudaMemcpyAsync(ea, at<float>(const_cast<void *>(workspace), h.layout.off_col), h.layout.n * 16,
+                                      cudaMemcpyDeviceToDevice, st))
         return SPLOTCH_ERR_CUDA;
     return SPLOTCH_OK;
 }

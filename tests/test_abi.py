@@ -73,7 +73,7 @@ def test_workspace_size_and_arguments(S):
     small = S.splotch_workspace_size(1000, cam, p)
     big = S.splotch_workspace_size(10_000_000, cam, p)
     assert 0 < small < big
-    assert big >= 10_000_000 * (16 + 16 + 4 + 8 + 16 + 8)
+    assert big >= 10_000_000 * (32 + 4 + 8 + 16)   # record, key, box, two sort buffers
     for bad in (dict(tile=12), dict(batch=100), dict(mode=5), dict(trunc_f=0.0), dict(max_tile_entries=1 << 33)):
         q = S.make_params(**{**dict(mode=S.EMISSION, tile=16, batch=128, max_tile_entries=1024), **bad})
         out = ctypes.c_size_t()
