@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the emission, e2e and CPU legs")
+    ap.add_argument("--frames-only", type=int, default=0,
+                    help="set up the workload, run this many frames and exit (for profilers)")
     return ap.parse_args()
 
 
@@ -203,6 +205,13 @@ def main():
     fr = S.Frame(dp, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev)
     fr.render()                      # sizes the tile-entry capacity for this workload
     info = fr.info()
+    if args.frames_only:
+        for _ in range(args.frames_only):
+            fr.run()
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"frames": args.frames_only, "status": int(fr.info().status),
+                          "tile_entries": int(info.tile_entries)}))
+        return
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
