@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="skip the emission, e2e and CPU legs")
     ap.add_argument("--frames-only", type=int, default=0,
                     help="set up the workload, run this many frames and exit (for profilers)")
+    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batching", "serving"],
+                    help="plain: the headline frame; precision: 100M particles with FP16/BF16 intensity; "
+                         "batching: views and snapshots in one captured graph; serving: request loop over a "
+                         "resident 1024^3 set")
     return ap.parse_args()
 
 
@@ -162,6 +166,143 @@ def run_reference(args, world, rank):
     }), flush=True)
 
 
+def time_frames(fr, steps, warmup, stream):
+    """Median and mean frame time (ms) of `steps` frames after `warmup`."""
+    import numpy as np
+    import torch
+    for _ in range(warmup):
+        fr.run()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record(stream)
+        fr.run()
+        b.record(stream)
+    torch.cuda.synchronize()
+    t = [a.elapsed_time(b) for a, b in ev]
+    return float(np.median(t)), float(np.mean(t))
+
+
+def run_precision(args, dev):
+    """Precision form: 100M clustered particles, intensity stored as FP32,
+    FP16 or BF16 (positions and h FP32, FP32 accumulation), absorptive
+    1920x1080.  Error against the FP64 oracle on a 1M-particle subsample:
+    fed the same rounded intensities (compute error) and the unrounded ones
+    (representation error)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from oracle import oracle as O
+    from paper_1004_1302_gb300 import splotch as S
+    ps, cam = synth.config2()
+    pal = synth.colormap()
+    stream = torch.cuda.current_stream(dev)
+    out = {"form": "precision", "metric": "particles rendered/s (1920x1080, absorptive)", "unit": "particles/s",
+           "config": {"workload": "config2: 100M particles, 5000 Plummer spheres + 10% uniform, 1920x1080, absorptive",
+                      "particles": ps.n}, "dtypes": {}}
+    for dtype in ("f32", "f16", "bf16"):
+        dp = S.upload(ps, dev, dtype)
+        fr = S.Frame(dp, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev)
+        fr.render()
+        med, mean = time_frames(fr, args.steps, max(args.warmup, 3), stream)
+        inf = fr.info()
+        out["dtypes"][dtype] = {"value": ps.n / (mean * 1e-3), "ms_per_step": mean, "p50_ms": med,
+                                "input_bytes_per_particle": 16 + (4 if dtype == "f32" else 2),
+                                "tile_entries": int(inf.tile_entries)}
+        del fr, dp
+        torch.cuda.empty_cache()
+    sub = ps.subsample(100)
+    ref32 = O.render_frame(sub, cam, pal, O.ABSORPTIVE, tile=16).image
+    top = np.abs(ref32).reshape(-1, 3).max(0)
+    err = {}
+    for dtype in ("f32", "f16", "bf16"):
+        dp = S.upload(sub, dev, dtype)
+        fr = S.Frame(dp, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev)
+        img = fr.render().cpu().numpy().astype(np.float64)
+        v = S.rounded_intensity(sub, dtype)
+        ref = O.render_frame(synth.ParticleSet(sub.x, sub.y, sub.z, sub.h, v, sub.species), cam, pal,
+                             O.ABSORPTIVE, tile=16).image
+        d_c, d_r = np.abs(img - ref), np.abs(img - ref32)
+        err[dtype] = {"compute_maxabs_over_max": (d_c.reshape(-1, 3).max(0) / top).max(),
+                      "compute_rms_over_max": (np.sqrt((d_c ** 2).reshape(-1, 3).mean(0)) / top).max(),
+                      "representation_maxabs_over_max": (d_r.reshape(-1, 3).max(0) / top).max(),
+                      "representation_rms_over_max": (np.sqrt((d_r ** 2).reshape(-1, 3).mean(0)) / top).max()}
+        del fr, dp
+    out["error_1M_subsample"] = {k: {kk: float(vv) for kk, vv in e.items()} for k, e in err.items()}
+    out["error_sample"] = f"every 100th particle ({sub.n}), full 1920x1080 frame, vs the FP64 oracle"
+    return out
+
+
+def run_batching(args, dev):
+    """Batching form: 64 orbit views (uniform azimuth steps) of the 10M
+    two-species set at 1024x1024, absorptive, plus 32 independent snapshots
+    of 10k-2M particles (log-uniform counts) at 512x512, emission.  Tile
+    size, renderer batch and split threshold come from the autotuner.  The
+    same frames are timed launched one by one from the host (plain) and as
+    one captured CUDA graph with a persistent render (batched)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1004_1302_gb300 import autotune as AT
+    from paper_1004_1302_gb300 import splotch as S
+    from paper_1004_1302_gb300.batch import BatchRenderer
+    pal = synth.colormap()
+    ps, _ = synth.config1(width=1024, height=1024)
+    dp = S.upload(ps, dev, "f32")
+    views = [synth.orbit_camera(k, 64, 1024, 1024) for k in range(64)]
+    sizes = synth.snapshot_sizes(32)
+    snaps = [synth.snapshot(k, n) for k, n in enumerate(sizes)]
+    dsnaps = [S.upload(sp, dev, "f32") for sp, _ in snaps]
+    tv = AT.autotune(dp, views[0], pal, S.ABSORPTIVE, device=dev, use_cache=False)
+    big = int(np.argmax(sizes))
+    tsn = AT.autotune(dsnaps[big], snaps[big][1], pal, S.EMISSION, device=dev, use_cache=False,
+                      tiles=(tv["tile"],), batches=(tv["batch"],))
+    jobs = [dict(particles=dp, camera=v, palette=pal, mode=S.ABSORPTIVE, large_threshold_px=tv["large_threshold_px"])
+            for v in views]
+    jobs += [dict(particles=d, camera=c, palette=pal, mode=S.EMISSION, large_threshold_px=tsn["large_threshold_px"])
+             for d, (_, c) in zip(dsnaps, snaps)]
+    br = BatchRenderer(jobs, tile=tv["tile"], batch=tv["batch"], device=dev)
+    br.prepare()
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    def plain():
+        for f in br.frames:
+            f.run()
+
+    t_plain = timed(plain, args.steps)
+    plain_imgs = [im.clone() for im in br.images()]
+    br.capture()
+    t_graph = timed(br.replay, args.steps)
+    same = all(torch.equal(x, y) for x, y in zip(plain_imgs, br.images()))
+    ok = all(st == 0 for st in br.statuses())
+    n_frames = len(br.frames)
+    return {"form": "batching", "metric": "frames/s and particles rendered/s of the batch", "unit": "particles/s",
+            "config": {"workload": "config3: 64 orbit views of the 10M set at 1024^2 (absorptive) + 32 snapshots "
+                                   "of 10k-2M particles at 512^2 (emission)", "frames": n_frames,
+                       "particles": br.particles, "tile": tv["tile"], "batch": tv["batch"],
+                       "view_threshold_px": tv["large_threshold_px"], "snapshot_threshold_px": tsn["large_threshold_px"]},
+            "plain": {"ms_per_batch": t_plain, "frames_per_s": n_frames / (t_plain * 1e-3),
+                      "value": br.particles / (t_plain * 1e-3)},
+            "batched": {"ms_per_batch": t_graph, "frames_per_s": n_frames / (t_graph * 1e-3),
+                        "value": br.particles / (t_graph * 1e-3)},
+            "speedup": t_plain / t_graph, "images_identical": bool(same), "status_ok": bool(ok),
+            "autotune_view": {k: tv[k] for k in ("tile", "batch", "large_threshold_px", "ms")},
+            "autotune_trials": len(tv["trials"])}
+
+
 def cpu_baseline(ps, cam, pal):
     import synth  # noqa: F401
     from oracle import oracle as O
@@ -198,6 +339,12 @@ def main():
     if world > 1:
         dist.barrier()
     S.load()
+    if args.form != "plain":
+        runner = {"precision": run_precision, "batching": run_batching}[args.form]
+        res = runner(args, dev)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return
 
     ps, cam = synth.config1()
     pal = synth.colormap()

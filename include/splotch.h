@@ -225,6 +225,39 @@ int splotch_get_tile_lists(const void *workspace, size_t workspace_bytes, uint32
 int splotch_get_colors(const void *workspace, size_t workspace_bytes, float *ea, void *stream);
 
 /*
+ * One frame of a batch render: a workspace that has been through
+ * splotch_transform, splotch_colorize, splotch_sort and splotch_bin for n
+ * particles with this camera, mode, max_tile_entries and the batch's tile
+ * size, and the frame's image (device, height x width x 3 floats).
+ */
+typedef struct {
+    uint64_t n;
+    const splotch_camera *camera;   /* host */
+    int32_t mode;                   /* splotch_mode of this frame */
+    int32_t reserved;
+    uint64_t max_tile_entries;
+    void *workspace;
+    size_t workspace_bytes;
+    float *image;
+} splotch_batch_item;
+
+#define SPLOTCH_MAX_BATCH 128
+
+/*
+ * Tile render of up to SPLOTCH_MAX_BATCH frames (views of one particle set,
+ * or independent snapshots) in one persistent launch: as many CTAs as fit on
+ * the GPU take (frame, tile) tasks from `counter` (device, one uint32 owned
+ * by the caller; zeroed by this call on `stream`), larger frames first.  Each
+ * frame's image equals what splotch_render_tiles gives for it.  The frames'
+ * workspaces must be distinct.  Makes no allocation and no host
+ * synchronisation, so a sequence of these calls can be captured in a CUDA
+ * graph.  SPLOTCH_ERR_ARG for a bad item, a tile size other than 8, 16 or
+ * 32, or more than SPLOTCH_MAX_BATCH items.
+ */
+int splotch_render_tiles_batch(const splotch_batch_item *items, int32_t n_items, int32_t tile, int32_t batch,
+                               uint32_t *counter, void *stream);
+
+/*
  * Measurement helpers.
  * splotch_count_fragments: enqueues a count, over the visible particles of
  *   the last transform, of the (pixel, particle) pairs that pass the

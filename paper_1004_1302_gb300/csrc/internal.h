@@ -120,6 +120,21 @@ struct RenderArgs {
     int width, height, tile, ntx, mode, batch;
 };
 
+// Render of many frames in one persistent launch: per frame its render
+// arguments and the index of its first (frame, tile) task.
+constexpr int kMaxBatchItems = 128;
+struct BatchItemArgs {
+    RenderArgs args;
+    uint32_t task_begin;
+    uint32_t pad;
+};
+struct BatchArgs {
+    unsigned int *counter;     // task counter (zeroed before the launch)
+    int n_items;
+    uint32_t n_tasks;
+    BatchItemArgs item[kMaxBatchItems];
+};
+
 // Layout of a workspace for n particles with this camera/params.
 int compute_layout(uint64_t n, int width, int height, int tile, uint64_t cap, Layout *out);
 
@@ -141,5 +156,7 @@ cudaError_t launch_sort_finish(Header *hdr, cudaStream_t st);   // absorptive or
 cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStream_t st);
 cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float *image, cudaStream_t st);
 cudaError_t launch_count_fragments(void *ws, const Layout &L, uint64_t *out, cudaStream_t st);
+RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, float *image);
+cudaError_t launch_render_batch(const BatchArgs &b, int tile, int batch, cudaStream_t st);
 
 }  // namespace spl

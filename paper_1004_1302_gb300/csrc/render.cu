@@ -53,16 +53,24 @@ __device__ __forceinline__ float2 q_series(float2 yn) {
 // {-sx, -sx, -sy, -sy}, {k, k, -A, -A}, {Er, Er, Eg, Eg}, {Eb, Eb, r2, A}
 // with k = -log2(e)/sigma_pix^2.
 
+template <int B> struct RenderSmem {
+    float4 s0[2][B], s1[2][B], s2[2][B], s3[2][B];
+    float4 scull[2][B];   // sx, sy, r2 for the cull test
+};
+
+// One screen tile, rendered by the whole CTA (all threads must call it).
 template <int T, int MODE, int B>
-__global__ void __launch_bounds__(T * T / 2) k_render(RenderArgs a) {
+__device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile, RenderSmem<B> &sm) {
     constexpr int kThreads = T * T / 2;
     constexpr int WX = 8, WY = 8;               // pixel block of one warp (two pixels per lane)
     constexpr int kWarpCols = T / WX;
     constexpr int kPer = (B + kThreads - 1) / kThreads;
-    __shared__ __align__(16) float4 s0[2][B], s1[2][B], s2[2][B], s3[2][B];
-    __shared__ __align__(16) float4 scull[2][B];   // sx, sy, r2 for the cull test
+    auto &s0 = sm.s0;
+    auto &s1 = sm.s1;
+    auto &s2 = sm.s2;
+    auto &s3 = sm.s3;
+    auto &scull = sm.scull;
 
-    const int tile = blockIdx.x;
     const int tx = tile % a.ntx, ty = tile / a.ntx;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wx0 = tx * T + (warp % kWarpCols) * WX, wy0 = ty * T + (warp / kWarpCols) * WY;
@@ -181,6 +189,39 @@ __global__ void __launch_bounds__(T * T / 2) k_render(RenderArgs a) {
     }
 }
 
+template <int T, int MODE, int B>
+__global__ void __launch_bounds__(T * T / 2) k_render(RenderArgs a) {
+    __shared__ __align__(16) RenderSmem<B> sm;
+    render_tile<T, MODE, B>(a, blockIdx.x, sm);
+}
+
+// Persistent render of the tiles of many frames: each CTA takes the next
+// (frame, tile) task from a counter until none is left.  Frames come in the
+// order of the table (the host puts the heaviest first), so the small ones
+// fill the tail.
+template <int T, int B>
+__global__ void __launch_bounds__(T * T / 2) k_render_batch(const __grid_constant__ BatchArgs args) {
+    __shared__ __align__(16) RenderSmem<B> sm;
+    __shared__ uint32_t s_task;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_task = atomicAdd(args.counter, 1u);
+        __syncthreads();
+        const uint32_t task = s_task;
+        if (task >= args.n_tasks) break;
+        int lo = 0, hi = args.n_items;   // last item whose first task is <= task
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (args.item[mid].task_begin <= task) lo = mid; else hi = mid;
+        }
+        const RenderArgs &a = args.item[lo].args;
+        const int tile = (int)(task - args.item[lo].task_begin);
+        if (a.mode == SPLOTCH_EMISSION) render_tile<T, SPLOTCH_EMISSION, B>(a, tile, sm);
+        else if (a.mode == SPLOTCH_ABSORPTIVE) render_tile<T, SPLOTCH_ABSORPTIVE, B>(a, tile, sm);
+        else render_tile<T, SPLOTCH_E_EQ_A, B>(a, tile, sm);
+    }
+}
+
 template <int T, int MODE>
 static void launch_tb(const RenderArgs &a, int ntiles, cudaStream_t st) {
     switch (a.batch) {
@@ -199,7 +240,7 @@ static void launch_t(const RenderArgs &a, int ntiles, cudaStream_t st) {
     }
 }
 
-cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float *image, cudaStream_t st) {
+RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, float *image) {
     int bits = 0;
     while (bits < 32 && (1ull << bits) < (unsigned long long)L.ntiles) ++bits;
     const int passes = (bits + 7) / 8;
@@ -216,6 +257,11 @@ cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float 
     a.ntx = L.ntx;
     a.mode = mode;
     a.batch = batch;
+    return a;
+}
+
+cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float *image, cudaStream_t st) {
+    const RenderArgs a = make_render_args(ws, L, mode, batch, image);
     switch (L.tile) {
     case 8: launch_t<8>(a, (int)L.ntiles, st); break;
     case 32: launch_t<32>(a, (int)L.ntiles, st); break;
@@ -223,6 +269,40 @@ cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float 
     }
     count_launches(1);
     return cudaGetLastError();
+}
+
+// Grid of the persistent batch render: as many CTAs as fit on the GPU at once.
+template <int T, int B>
+static cudaError_t launch_batch_tb(const BatchArgs &b, cudaStream_t st) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_batch<T, B>, T * T / 2, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    k_render_batch<T, B><<<sms * per_sm, T * T / 2, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+template <int T>
+static cudaError_t launch_batch_t(const BatchArgs &b, int batch, cudaStream_t st) {
+    switch (batch) {
+    case 64: return launch_batch_tb<T, 64>(b, st);
+    case 128: return launch_batch_tb<T, 128>(b, st);
+    default: return launch_batch_tb<T, 256>(b, st);
+    }
+}
+
+cudaError_t launch_render_batch(const BatchArgs &b, int tile, int batch, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    switch (tile) {
+    case 8: e = launch_batch_t<8>(b, batch, st); break;
+    case 32: e = launch_batch_t<32>(b, batch, st); break;
+    default: e = launch_batch_t<16>(b, batch, st); break;
+    }
+    count_launches(1);
+    return e;
 }
 
 // Number of (pixel, particle) pairs that pass the membership test, summed

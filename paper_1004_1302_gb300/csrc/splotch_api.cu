@@ -1,9 +1,12 @@
 // C ABI of the library: argument checks, workspace layout and the order in
 // which each call enqueues its kernels.  See include/splotch.h for the
 // contract of every entry point.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <numeric>
+#include <vector>
 
 #include "internal.h"
 
@@ -276,6 +279,34 @@ int splotch_render_tiles(const splotch_render_params *params, const splotch_came
     if (!image) return SPLOTCH_ERR_ARG;
     return cuda_status(launch_render(workspace, L, params->mode, params->batch, image,
                                      static_cast<cudaStream_t>(stream)));
+}
+
+int splotch_render_tiles_batch(const splotch_batch_item *items, int32_t n_items, int32_t tile, int32_t batch,
+                               uint32_t *counter, void *stream) {
+    if (!items || n_items < 1 || n_items > kMaxBatchItems || !counter) return SPLOTCH_ERR_ARG;
+    if (!(tile == 8 || tile == 16 || tile == 32) || !(batch == 64 || batch == 128 || batch == 256))
+        return SPLOTCH_ERR_ARG;
+    std::vector<int> order(n_items);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return items[a].n > items[b].n; });
+    static thread_local BatchArgs b;   // ~10 KB: kept off the stack
+    b.counter = counter;
+    b.n_items = n_items;
+    uint64_t tasks = 0;
+    for (int k = 0; k < n_items; ++k) {
+        const splotch_batch_item &it = items[order[k]];
+        if (check_camera(it.camera) || it.mode < 0 || it.mode > 2 || !it.image) return SPLOTCH_ERR_ARG;
+        Layout L;
+        int s = compute_layout(it.n, it.camera->width, it.camera->height, tile, it.max_tile_entries, &L);
+        if (s) return s;
+        if ((s = check_ws(it.workspace, it.workspace_bytes, L))) return s;
+        b.item[k].args = make_render_args(it.workspace, L, it.mode, batch, it.image);
+        b.item[k].task_begin = (uint32_t)tasks;
+        tasks += L.ntiles;
+        if (tasks >= (1ull << 32)) return SPLOTCH_ERR_ARG;
+    }
+    b.n_tasks = (uint32_t)tasks;
+    return cuda_status(launch_render_batch(b, tile, batch, static_cast<cudaStream_t>(stream)));
 }
 
 int splotch_render(const splotch_render_params *params, const splotch_camera *cam, uint64_t n, void *workspace,

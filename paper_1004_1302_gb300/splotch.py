@@ -102,6 +102,15 @@ class RenderParams(ctypes.Structure):
                 ("max_tile_entries", ctypes.c_uint64)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("camera", ctypes.c_void_p), ("mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("max_tile_entries", ctypes.c_uint64), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t), ("image", ctypes.c_void_p)]
+
+
+MAX_BATCH = 128
+
+
 class FrameInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("visible", ctypes.c_uint32), ("tile_entries", ctypes.c_uint64),
                 ("large", ctypes.c_uint32), ("ntiles", ctypes.c_uint32), ("lo", ctypes.c_float * MAX_SPECIES),
@@ -112,7 +121,7 @@ EXPORTS = ["splotch_abi_version", "splotch_status_string", "splotch_camera_init"
            "splotch_transform", "splotch_colorize", "splotch_render", "splotch_sort", "splotch_bin",
            "splotch_render_tiles", "splotch_frame_info", "splotch_get_keys", "splotch_get_geometry",
            "splotch_get_order", "splotch_get_tile_lists", "splotch_get_colors", "splotch_count_fragments",
-           "splotch_launch_count", "splotch_sort_keys_no_alloc"]
+           "splotch_launch_count", "splotch_sort_keys_no_alloc", "splotch_render_tiles_batch"]
 
 _lib = None
 
@@ -147,6 +156,7 @@ def load(path: str | None = None):
         "splotch_count_fragments": ([P(RenderParams), P(Camera), U64, V, ctypes.c_size_t, V, V], I32),
         "splotch_launch_count": ([], U64),
         "splotch_sort_keys_no_alloc": ([V, ctypes.c_uint32, V, V, V], I32),
+        "splotch_render_tiles_batch": ([P(BatchItem), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, V, V], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -241,6 +251,13 @@ def splotch_get_colors(ws, ws_bytes, ea, stream):
 def splotch_count_fragments(params, cam, n, ws, ws_bytes, out, stream):
     _check(load().splotch_count_fragments(ctypes.byref(params), ctypes.byref(cam), n, ws, ws_bytes, out, stream),
            "splotch_count_fragments")
+
+
+def splotch_render_tiles_batch(items, tile: int, batch: int, counter: int, stream: int):
+    """Persistent tile render of up to MAX_BATCH prepared frames (BatchItem list)."""
+    arr = (BatchItem * len(items))(*items)
+    _check(load().splotch_render_tiles_batch(arr, len(items), tile, batch, counter, stream),
+           "splotch_render_tiles_batch")
 
 
 NO_ALLOC_MAX_KEYS = 1 << 18
