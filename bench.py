@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the emission, e2e and CPU legs")
+    ap.add_argument("--requests", type=int, default=200, help="serving form: number of requests")
+    ap.add_argument("--lattice", type=int, default=1024, help="serving form: side of the resident lattice")
     ap.add_argument("--frames-only", type=int, default=0,
                     help="set up the workload, run this many frames and exit (for profilers)")
     ap.add_argument("--form", default="plain", choices=["plain", "precision", "batching", "serving"],
@@ -303,6 +305,75 @@ def run_batching(args, dev):
             "autotune_trials": len(tv["trials"])}
 
 
+def resident_lattice(n_side, dev, chunk=1 << 25):
+    """The n_side^3 displaced lattice with overdensities, generated in slices
+    straight into device arrays: FP32 position and h, FP16 intensity."""
+    import torch
+
+    import synth
+    from paper_1004_1302_gb300 import splotch as S
+    n = n_side ** 3
+    cols = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(4)]
+    v = torch.empty(n, dtype=torch.float16, device=dev)
+    for i0 in range(0, n, chunk):
+        m = min(chunk, n - i0)
+        arrs = synth.lattice(n_side, i0, m)
+        for t, a in zip(cols, arrs[:4]):
+            t[i0:i0 + m].copy_(torch.from_numpy(a))
+        v[i0:i0 + m].copy_(torch.from_numpy(arrs[4]).to(dev).to(torch.float16))
+    sp = synth.Species(0, n, use_log=1, brightness=0.02, absorption=0.05)
+    return S.DeviceParticles(*cols, v, "f16", [sp])
+
+
+def run_serving(args, dev):
+    """Serving form: a 1024^3 (1.07e9) particle set resident on the device
+    (FP32 position/h, FP16 intensity; 18 B per particle).  First the whole set
+    as one 1920x1080 absorptive frame; then a Poisson stream of requests, each
+    a region-of-interest cut of 1M-300M particles at 512^2 to 3840x2160 with a
+    random camera, admitted by memory and overlapped on the device."""
+    import torch
+
+    import synth
+    from paper_1004_1302_gb300 import splotch as S
+    from paper_1004_1302_gb300.serve import RenderServer, poisson_arrivals, random_requests
+    t0 = time.perf_counter()
+    res = resident_lattice(args.lattice, dev)
+    torch.cuda.synchronize(dev)
+    t_gen = time.perf_counter() - t0
+    pal = synth.colormap()
+    out = {"form": "serving", "metric": "requests/s, particles rendered/s and p50/p99 latency", "unit": "particles/s",
+           "config": {"workload": f"config4: {args.lattice}^3 displaced lattice + 10000 Plummer overdensities, "
+                                  "FP32 pos/h + FP16 intensity, resident", "particles": res.n,
+                      "resident_bytes": res.n * 18, "generate_and_upload_s": t_gen}}
+    # whole set, one 1920x1080 absorptive frame
+    cam = synth.CameraSpec((0.5, 0.5, -1.5), (0.5, 0.5, 0.5), (0.0, 1.0, 0.0), 45.0, 1920, 1080)
+    fr = S.Frame(res, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev,
+                 max_tile_entries=int(2.2 * res.n))
+    fr.render()
+    med, mean = time_frames(fr, 3, 1, torch.cuda.current_stream(dev))
+    inf = fr.info()
+    out["full_frame"] = {"particles": res.n, "ms": mean, "p50_ms": med, "value": res.n / (mean * 1e-3),
+                         "visible": int(inf.visible), "tile_entries": int(inf.tile_entries),
+                         "workspace_bytes": int(fr.ws_bytes), "status": int(inf.status)}
+    del fr
+    torch.cuda.empty_cache()
+    # request stream
+    server = RenderServer(res, pal, res.species[0], tile=args.tile, batch=args.batch, max_inflight=8, device=dev)
+    reqs = random_requests(args.requests, res.n)
+    calib = reqs[:min(16, len(reqs))]
+    for r in calib:
+        r.arrival = 0.0
+    done, st = server.serve(calib)
+    capacity = st["frames_per_s"]
+    rest = poisson_arrivals(random_requests(args.requests, res.n, seed=0x5E21), 0.7 * capacity)
+    done, st = server.serve(rest)
+    out["calibration"] = {"requests": len(calib), "saturated_frames_per_s": capacity}
+    out["serving"] = dict(st, arrival_rate_per_s=0.7 * capacity, budget_bytes=server.budget,
+                          peak_reserved_bytes=server.peak_in_use)
+    out["value"] = st["particles_per_s"]
+    return out
+
+
 def cpu_baseline(ps, cam, pal):
     import synth  # noqa: F401
     from oracle import oracle as O
@@ -340,7 +411,7 @@ def main():
         dist.barrier()
     S.load()
     if args.form != "plain":
-        runner = {"precision": run_precision, "batching": run_batching}[args.form]
+        runner = {"precision": run_precision, "batching": run_batching, "serving": run_serving}[args.form]
         res = runner(args, dev)
         if rank == 0:
             print(json.dumps(res), flush=True)

@@ -258,6 +258,25 @@ int splotch_render_tiles_batch(const splotch_batch_item *items, int32_t n_items,
                                uint32_t *counter, void *stream);
 
 /*
+ * Region-of-interest cut of a resident particle set (serving): the particles
+ * of `src` inside the box {x_lo, y_lo, z_lo, x_hi, y_hi, z_hi}, i.e. with
+ * lo <= p < hi on every axis (compared in single precision, bounds rounded
+ * to float), copied in index order.  Only x, y, z, h and the intensity are
+ * copied; species ranges of `src` are not tracked (cut one range at a time).
+ * scratch: device, at least splotch_roi_scratch_size bytes, caller-owned.
+ * splotch_roi_count writes the number of particles inside to *count (device
+ * uint64).  splotch_roi_select also writes the first min(count, capacity)
+ * of them to x, y, z, h (device floats) and intensity (device, src's dtype).
+ * Both are asynchronous on `stream` and allocate nothing.
+ */
+int splotch_roi_scratch_size(uint64_t n, size_t *bytes);
+int splotch_roi_count(const splotch_particles *src, const double box[6], void *scratch, size_t scratch_bytes,
+                      uint64_t *count, void *stream);
+int splotch_roi_select(const splotch_particles *src, const double box[6], void *scratch, size_t scratch_bytes,
+                       float *x, float *y, float *z, float *h, void *intensity, uint64_t capacity, uint64_t *count,
+                       void *stream);
+
+/*
  * Measurement helpers.
  * splotch_count_fragments: enqueues a count, over the visible particles of
  *   the last transform, of the (pixel, particle) pairs that pass the

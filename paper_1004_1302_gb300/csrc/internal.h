@@ -158,5 +158,8 @@ cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float 
 cudaError_t launch_count_fragments(void *ws, const Layout &L, uint64_t *out, cudaStream_t st);
 RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, float *image);
 cudaError_t launch_render_batch(const BatchArgs &b, int tile, int batch, cudaStream_t st);
+uint32_t roi_ctas(uint64_t n);
+cudaError_t launch_roi(const splotch_particles *p, const double box[6], void *scratch, uint64_t *count, float *ox,
+                       float *oy, float *oz, float *oh, void *ov, uint64_t capacity, bool scatter, cudaStream_t st);
 
 }  // namespace spl

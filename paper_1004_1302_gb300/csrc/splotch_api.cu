@@ -309,6 +309,39 @@ int splotch_render_tiles_batch(const splotch_batch_item *items, int32_t n_items,
     return cuda_status(launch_render_batch(b, tile, batch, static_cast<cudaStream_t>(stream)));
 }
 
+int splotch_roi_scratch_size(uint64_t n, size_t *bytes) {
+    if (!bytes || n >= (1ull << 32)) return SPLOTCH_ERR_ARG;
+    *bytes = (size_t)kMaxSortCtas * 8;
+    return SPLOTCH_OK;
+}
+
+static int check_roi(const splotch_particles *src, const double box[6], const void *scratch, size_t scratch_bytes,
+                     const uint64_t *count) {
+    if (!src || !box || !scratch || !count || src->n >= (1ull << 32)) return SPLOTCH_ERR_ARG;
+    if (src->n && (!src->x || !src->y || !src->z || !src->h || !src->intensity)) return SPLOTCH_ERR_ARG;
+    if (src->intensity_dtype < 0 || src->intensity_dtype > 2) return SPLOTCH_ERR_ARG;
+    if (scratch_bytes < (size_t)kMaxSortCtas * 8) return SPLOTCH_ERR_WORKSPACE;
+    return SPLOTCH_OK;
+}
+
+int splotch_roi_count(const splotch_particles *src, const double box[6], void *scratch, size_t scratch_bytes,
+                      uint64_t *count, void *stream) {
+    int s = check_roi(src, box, scratch, scratch_bytes, count);
+    if (s) return s;
+    return cuda_status(launch_roi(src, box, scratch, count, nullptr, nullptr, nullptr, nullptr, nullptr, 0, false,
+                                  static_cast<cudaStream_t>(stream)));
+}
+
+int splotch_roi_select(const splotch_particles *src, const double box[6], void *scratch, size_t scratch_bytes,
+                       float *x, float *y, float *z, float *h, void *intensity, uint64_t capacity, uint64_t *count,
+                       void *stream) {
+    int s = check_roi(src, box, scratch, scratch_bytes, count);
+    if (s) return s;
+    if (capacity && (!x || !y || !z || !h || !intensity)) return SPLOTCH_ERR_ARG;
+    return cuda_status(launch_roi(src, box, scratch, count, x, y, z, h, intensity, capacity, true,
+                                  static_cast<cudaStream_t>(stream)));
+}
+
 int splotch_render(const splotch_render_params *params, const splotch_camera *cam, uint64_t n, void *workspace,
                    size_t workspace_bytes, float *image, void *stream) {
     if (!image) return SPLOTCH_ERR_ARG;

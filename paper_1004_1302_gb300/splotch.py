@@ -19,7 +19,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "_splotch.so")
-SOURCES = ["splotch_api.cu", "transform.cu", "sort.cu", "bin.cu", "render.cu", "no_alloc.cu"]
+SOURCES = ["splotch_api.cu", "transform.cu", "sort.cu", "bin.cu", "render.cu", "roi.cu", "no_alloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 OK, ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_TIMEOUT, ERR_OOM_ADMISSION, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
@@ -121,7 +121,8 @@ EXPORTS = ["splotch_abi_version", "splotch_status_string", "splotch_camera_init"
            "splotch_transform", "splotch_colorize", "splotch_render", "splotch_sort", "splotch_bin",
            "splotch_render_tiles", "splotch_frame_info", "splotch_get_keys", "splotch_get_geometry",
            "splotch_get_order", "splotch_get_tile_lists", "splotch_get_colors", "splotch_count_fragments",
-           "splotch_launch_count", "splotch_sort_keys_no_alloc", "splotch_render_tiles_batch"]
+           "splotch_launch_count", "splotch_sort_keys_no_alloc", "splotch_render_tiles_batch",
+           "splotch_roi_scratch_size", "splotch_roi_count", "splotch_roi_select"]
 
 _lib = None
 
@@ -157,6 +158,9 @@ def load(path: str | None = None):
         "splotch_launch_count": ([], U64),
         "splotch_sort_keys_no_alloc": ([V, ctypes.c_uint32, V, V, V], I32),
         "splotch_render_tiles_batch": ([P(BatchItem), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, V, V], I32),
+        "splotch_roi_scratch_size": ([U64, P(ctypes.c_size_t)], I32),
+        "splotch_roi_count": ([P(Particles), P(ctypes.c_double), V, ctypes.c_size_t, V, V], I32),
+        "splotch_roi_select": ([P(Particles), P(ctypes.c_double), V, ctypes.c_size_t, V, V, V, V, V, U64, V, V], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -258,6 +262,27 @@ def splotch_render_tiles_batch(items, tile: int, batch: int, counter: int, strea
     arr = (BatchItem * len(items))(*items)
     _check(load().splotch_render_tiles_batch(arr, len(items), tile, batch, counter, stream),
            "splotch_render_tiles_batch")
+
+
+def splotch_roi_scratch_size(n: int) -> int:
+    out = ctypes.c_size_t()
+    _check(load().splotch_roi_scratch_size(n, ctypes.byref(out)), "splotch_roi_scratch_size")
+    return out.value
+
+
+def _box(box):
+    return (ctypes.c_double * 6)(*[float(v) for v in box])
+
+
+def splotch_roi_count(src: Particles, box, scratch: int, scratch_bytes: int, count: int, stream: int):
+    _check(load().splotch_roi_count(ctypes.byref(src), _box(box), scratch, scratch_bytes, count, stream),
+           "splotch_roi_count")
+
+
+def splotch_roi_select(src: Particles, box, scratch: int, scratch_bytes: int, x, y, z, h, v, capacity: int,
+                       count: int, stream: int):
+    _check(load().splotch_roi_select(ctypes.byref(src), _box(box), scratch, scratch_bytes, x, y, z, h, v, capacity,
+                                     count, stream), "splotch_roi_select")
 
 
 NO_ALLOC_MAX_KEYS = 1 << 18
