@@ -115,7 +115,8 @@ typedef struct {
 typedef struct {
     int32_t status;               /* device-side status (splotch_status) */
     uint32_t visible;             /* V: particles that reach the image */
-    uint64_t tile_entries;        /* D: sum over visible particles of tiles touched */
+    uint64_t tile_entries;        /* D: sum over visible particles of tiles touched (after a capacity
+                                     overflow: a lower bound to grow max_tile_entries to) */
     uint32_t large;               /* particles sent to the cooperative emission path */
     uint32_t ntiles;
     float lo[SPLOTCH_MAX_SPECIES], hi[SPLOTCH_MAX_SPECIES];   /* normalisation range used */

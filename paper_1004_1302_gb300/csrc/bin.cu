@@ -1,11 +1,20 @@
-// Screen-tile binning.  Every visible particle, in render order, adds one
-// entry (tile id, particle) per tile its box meets.  Entry offsets come from
-// an exclusive scan of the per-particle tile counts, so the entries of one
-// particle sit at fixed positions whatever the thread that writes them.
-// Particles touching more tiles than a threshold are split over a whole CTA
-// (the "split particles" idea of Section 3.2 applied to the emission of
-// work items).  A stable radix sort by tile id then yields per-tile lists in
-// render order, and a boundary pass turns the sorted ids into tile offsets.
+// Screen-tile binning in two levels, without sorting per-tile entries.
+//
+// 1. Every visible particle, in render order, adds one entry (super-tile,
+//    particle) per super-tile (8 x 8 screen tiles) its box meets; offsets come
+//    from a scan of the per-particle counts, so entries sit at fixed places.
+//    Particles touching more super-tiles than a threshold are written by a
+//    whole warp (the "split particles" idea of Section 3.2 applied to the
+//    emission of work items).
+// 2. One stable radix pass groups the entries by super-tile, keeping render
+//    order inside each group.
+// 3. Each super-tile's list is cut into units of kUnit entries.  A particle's
+//    footprint inside its super-tile is a 64-bit mask of fine tiles; per unit
+//    the fine-tile counts come from ballots, a scan over units and over fine
+//    tiles gives every (unit, fine tile) its output position, and the same
+//    ballots give each entry its rank among the earlier entries of its warp.
+//    The result is, for every fine tile (row-major), the particles whose box
+//    meets it in render order: bit-exact, as a stable sort by tile would give.
 #include "internal.h"
 #include "device_util.cuh"
 
@@ -13,8 +22,9 @@ namespace spl {
 
 constexpr int kBinStep = 2048;   // particles per CTA step of the emission kernel
 
-__device__ __forceinline__ uint32_t tiles_of(const ushort4 b, int tshift) {
-    return (uint32_t)((b.z >> tshift) - (b.x >> tshift) + 1) * (uint32_t)((b.w >> tshift) - (b.y >> tshift) + 1);
+// Number of (super-)tiles of side 2^shift pixels that a pixel box meets.
+__device__ __forceinline__ uint32_t cells_of(const ushort4 b, int shift) {
+    return (uint32_t)((b.z >> shift) - (b.x >> shift) + 1) * (uint32_t)((b.w >> shift) - (b.y >> shift) + 1);
 }
 
 __device__ __forceinline__ void bin_range(uint32_t ctas, uint32_t n, uint64_t *beg, uint64_t *end) {
@@ -33,7 +43,7 @@ __global__ void __launch_bounds__(256) k_bin_reduce(BinArgs a) {
     uint64_t beg, end;
     bin_range(a.ctas, n, &beg, &end);
     unsigned long long sum = 0;
-    for (uint64_t k = beg + threadIdx.x; k < end; k += blockDim.x) sum += tiles_of(a.box[list[k]], a.tshift);
+    for (uint64_t k = beg + threadIdx.x; k < end; k += blockDim.x) sum += cells_of(a.box[list[k]], a.sshift);
     unsigned long long tot;
     block_exclusive_scan64<256>(sum, ws, &tot);
     if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
@@ -58,23 +68,26 @@ __global__ void __launch_bounds__(1024) k_bin_scan(BinArgs a) {
         run += v[q];
     }
     if (threadIdx.x == 0) {
-        a.hdr->tile_entries = total;
-        a.hdr->tile_entries32 = (uint32_t)(total < a.cap ? total : a.cap);
-        if (total > a.cap) a.hdr->status = SPLOTCH_ERR_WORKSPACE;
+        a.hdr->super_entries = total;
+        a.hdr->super32 = (uint32_t)(total < a.cap ? total : a.cap);
+        if (total > a.cap) {
+            // the fine entries are at least as many: report that lower bound
+            a.hdr->status = SPLOTCH_ERR_WORKSPACE;
+            a.hdr->tile_entries = total;
+        }
     }
 }
 
-// Each CTA walks its range in steps of kBinStep particles (list order).
-// A particle touching at most `large_tiles` tiles is written by the thread
+// Each CTA walks its range in steps of kBinStep particles (list order).  A
+// particle meeting at most `large_tiles` super-tiles is written by the thread
 // that owns it; the step's larger particles are split over the CTA's warps,
-// one warp per particle with its lanes across a row of tiles, so the writes
-// of a row are contiguous.
+// one warp per particle with its lanes across a row of super-tiles.
 __global__ void __launch_bounds__(256) k_bin_emit(BinArgs a) {
     constexpr int kPer = kBinStep / 256;
     __shared__ uint32_t s_p[kBinStep];        // particle index per item
-    __shared__ uint32_t s_off[kBinStep];      // tiles per item, then its entry offset within the step
+    __shared__ uint32_t s_off[kBinStep];      // cells per item, then its entry offset within the step
     __shared__ uint32_t s_lidx[kBinStep];     // items of the large particles, in list order
-    __shared__ ushort4 s_box[kBinStep];       // tile box per item: tx0, ty0, tx1, ty1
+    __shared__ ushort4 s_box[kBinStep];       // super-tile box per item
     __shared__ uint32_t ws32[9];
     const uint32_t n = a.hdr->visible;
     const uint32_t *list = a.hdr->sorted_buf ? a.list[1] : a.list[0];
@@ -93,7 +106,7 @@ __global__ void __launch_bounds__(256) k_bin_emit(BinArgs a) {
             if (j < m) {
                 p = list[step + j];
                 const ushort4 b = a.box[p];
-                tb = make_ushort4(b.x >> a.tshift, b.y >> a.tshift, b.z >> a.tshift, b.w >> a.tshift);
+                tb = make_ushort4(b.x >> a.sshift, b.y >> a.sshift, b.z >> a.sshift, b.w >> a.sshift);
                 nt = (uint32_t)(tb.z - tb.x + 1) * (uint32_t)(tb.w - tb.y + 1);
             }
             s_p[j] = p;
@@ -132,11 +145,11 @@ __global__ void __launch_bounds__(256) k_bin_emit(BinArgs a) {
             for (int ty = b.y; ty <= b.w; ++ty)
                 for (int tx = b.x; tx <= b.z; ++tx, ++e)
                     if (e < a.cap) {
-                        a.ek[e] = (uint32_t)(ty * a.ntx + tx);
+                        a.ek[e] = (uint32_t)(ty * a.nsx + tx);
                         a.ev[e] = p;
                     }
         }
-        // large particles: one warp per particle, lanes across a row of tiles
+        // large particles: one warp per particle, lanes across a row
         for (uint32_t i = warp; i < ltot; i += 8) {
             const uint32_t j = s_lidx[i];
             const uint32_t p = s_p[j];
@@ -147,7 +160,7 @@ __global__ void __launch_bounds__(256) k_bin_emit(BinArgs a) {
                 for (uint32_t c = lane; c < w; c += 32) {
                     const unsigned long long e = e0 + c;
                     if (e < a.cap) {
-                        a.ek[e] = (uint32_t)(ty * a.ntx + b.x) + c;
+                        a.ek[e] = (uint32_t)(ty * a.nsx + b.x) + c;
                         a.ev[e] = p;
                     }
                 }
@@ -159,21 +172,174 @@ __global__ void __launch_bounds__(256) k_bin_emit(BinArgs a) {
     if (threadIdx.x == 0 && nlarge_cta) atomicAdd(&a.hdr->n_large, nlarge_cta);
 }
 
-// Tile offsets from tile-sorted entry ids: offsets[t] = first entry of tile t.
-__global__ void __launch_bounds__(256) k_tile_offsets(const Header *hdr, const uint32_t *ek, uint32_t *toff,
-                                                      uint32_t ntiles) {
-    const uint32_t D = hdr->tile_entries32;
+// Offsets of groups in a sequence sorted by group id: offsets[g] = first
+// entry of group g, offsets[ngroups] = n.
+__global__ void __launch_bounds__(256) k_group_offsets(const uint32_t *count, const uint32_t *ids, uint32_t *off,
+                                                       uint32_t ngroups) {
+    const uint32_t n = *count;
     const uint32_t stride = gridDim.x * blockDim.x;
-    if (D == 0) {
-        for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += stride) toff[t] = 0;
+    if (n == 0) {
+        for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t <= ngroups; t += stride) off[t] = 0;
         return;
     }
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < D; e += stride) {
-        const uint32_t t = ek[e];
-        const uint32_t prev = e ? ek[e - 1] + 1u : 0u;
-        for (uint32_t tt = prev; tt <= t; ++tt) toff[tt] = e;
-        if (e == D - 1)
-            for (uint32_t tt = t + 1; tt <= ntiles; ++tt) toff[tt] = D;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+        const uint32_t t = ids[e];
+        const uint32_t prev = e ? ids[e - 1] + 1u : 0u;
+        for (uint32_t tt = prev; tt <= t; ++tt) off[tt] = e;
+        if (e == n - 1)
+            for (uint32_t tt = t + 1; tt <= ngroups; ++tt) off[tt] = n;
+    }
+}
+
+// Fine tiles of super-tile s that a particle's pixel box meets, as a 64-bit
+// mask: bit 8 r + c for row r and column c inside the super-tile.
+__device__ __forceinline__ uint64_t fine_mask(const ushort4 b, int tshift, uint32_t s, uint32_t nsx) {
+    const int ox = (int)(s % nsx) * kSuperSide, oy = (int)(s / nsx) * kSuperSide;
+    const int c0 = max((b.x >> tshift) - ox, 0), c1 = min((b.z >> tshift) - ox, kSuperSide - 1);
+    const int r0 = max((b.y >> tshift) - oy, 0), r1 = min((b.w >> tshift) - oy, kSuperSide - 1);
+    if (c0 > c1 || r0 > r1) return 0ull;
+    const uint64_t row = (0xFFull >> (kSuperSide - 1 - c1)) & (0xFFull << c0);
+    uint64_t m = 0;
+    for (int r = r0; r <= r1; ++r) m |= row << (kSuperSide * r);
+    return m;
+}
+
+__device__ __forceinline__ uint64_t warp_or64(uint64_t m) {
+    const uint32_t lo = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)m);
+    const uint32_t hi = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)(m >> 32));
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// Cut every super-tile's list into units of at most kUnit entries.
+__global__ void __launch_bounds__(1024) k_units(FineArgs a) {
+    __shared__ uint32_t ws[33];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < a.nsuper; base += 1024) {
+        const uint32_t s = base + threadIdx.x;
+        uint32_t nseg = 0, b = 0, e = 0;
+        if (s < a.nsuper) {
+            b = a.soff[s];
+            e = a.soff[s + 1];
+            nseg = (e - b + kUnit - 1) / kUnit;
+        }
+        uint32_t tot;
+        const uint32_t pre = block_exclusive_scan<1024>(nseg, ws, &tot);
+        if (s < a.nsuper) {
+            const uint32_t u0 = carry + pre;
+            a.ufirst[s] = u0;
+            for (uint32_t k = 0; k < nseg && u0 + k < a.max_units; ++k)
+                a.units[u0 + k] = make_uint4(s, b + k * kUnit, min(b + (k + 1) * kUnit, e), 0u);
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        a.ufirst[a.nsuper] = carry;
+        a.hdr->n_units = min(carry, a.max_units);
+    }
+}
+
+// Per unit: how many of the unit's entries meet each of the super-tile's 64
+// fine tiles.
+__global__ void __launch_bounds__(256) k_fine_count(FineArgs a) {
+    __shared__ uint32_t cnt[64];
+    const uint32_t u = blockIdx.x;
+    if (u >= a.hdr->n_units) return;
+    const uint4 un = a.units[u];
+    if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t i = un.y + threadIdx.x; i < un.z; i += 256) {
+        uint64_t m = fine_mask(a.box[a.sval[i]], a.tshift, un.x, a.nsx);
+        while (m) {
+            atomicAdd(&cnt[__ffsll((long long)m) - 1], 1u);
+            m &= m - 1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) a.ucnt[(size_t)u * 64 + threadIdx.x] = cnt[threadIdx.x];
+}
+
+// Per super-tile: each fine tile's running count over the super-tile's units
+// (exclusive, in place) and its total, written as the fine tile's count.
+__global__ void __launch_bounds__(64) k_fine_unit_scan(FineArgs a) {
+    const uint32_t s = blockIdx.x, t = threadIdx.x;
+    uint32_t run = 0;
+    const uint32_t u1 = min(a.ufirst[s + 1], a.max_units);
+    for (uint32_t u = a.ufirst[s]; u < u1; ++u) {
+        const size_t q = (size_t)u * 64 + t;
+        const uint32_t c = a.ucnt[q];
+        a.ucnt[q] = run;
+        run += c;
+    }
+    const uint32_t tx = (s % a.nsx) * kSuperSide + (t % kSuperSide), ty = (s / a.nsx) * kSuperSide + t / kSuperSide;
+    if (tx < a.ntx && ty < a.nty) a.toff[ty * a.ntx + tx] = run;
+}
+
+// Fine-tile counts -> offsets (exclusive scan in place), total D.
+__global__ void __launch_bounds__(1024) k_fine_offsets(FineArgs a) {
+    __shared__ unsigned long long ws[33];
+    constexpr int kPer = 8;
+    unsigned long long carry = 0;
+    for (uint32_t base = 0; base < a.ntiles; base += 1024 * kPer) {
+        uint32_t v[kPer];
+        unsigned long long sum = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t j = base + threadIdx.x * kPer + q;
+            v[q] = j < a.ntiles ? a.toff[j] : 0u;
+            sum += v[q];
+        }
+        unsigned long long tot;
+        unsigned long long run = carry + block_exclusive_scan64<1024>(sum, ws, &tot);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t j = base + threadIdx.x * kPer + q;
+            if (j < a.ntiles) a.toff[j] = (uint32_t)(run < a.cap ? run : a.cap);
+            run += v[q];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        a.toff[a.ntiles] = (uint32_t)(carry < a.cap ? carry : a.cap);
+        // after an overflow of the super-tile entries the count is only a lower bound
+        const bool exact = a.hdr->status == SPLOTCH_OK;
+        a.hdr->tile_entries = exact || carry > a.hdr->tile_entries ? carry : a.hdr->tile_entries;
+        a.hdr->tile_entries32 = (uint32_t)(carry < a.cap ? carry : a.cap);
+        if (carry > a.cap) a.hdr->status = SPLOTCH_ERR_WORKSPACE;
+    }
+}
+
+// Per unit, one thread per fine tile: walk the unit's entries in order
+// (64 at a time: each thread stages one entry's particle and fine-tile mask
+// in shared memory, read back by broadcast) and append the
+// particle of every entry whose mask has the thread's tile, starting at the
+// tile's offset plus the unit's offset within the tile.  Render order is kept
+// because each tile's entries are appended in list order by one thread.
+__global__ void __launch_bounds__(64) k_fine_emit(FineArgs a) {
+    __shared__ uint64_t sm[64];
+    __shared__ uint32_t sp[64];
+    const uint32_t u = blockIdx.x;
+    if (u >= a.hdr->n_units) return;
+    const uint4 un = a.units[u];
+    const uint32_t s = un.x, t = threadIdx.x;
+    const uint32_t tx = (s % a.nsx) * kSuperSide + (t % kSuperSide), ty = (s / a.nsx) * kSuperSide + t / kSuperSide;
+    uint64_t pos = (tx < a.ntx && ty < a.nty) ? (uint64_t)a.toff[ty * a.ntx + tx] + a.ucnt[(size_t)u * 64 + t] : 0;
+    const uint32_t word = t >> 5, bit = t & 31;
+    for (uint32_t i0 = un.y; i0 < un.z; i0 += 64) {
+        const uint32_t i = i0 + t;
+        const uint32_t p = i < un.z ? a.sval[i] : 0u;
+        sm[t] = i < un.z ? fine_mask(a.box[p], a.tshift, s, a.nsx) : 0ull;
+        sp[t] = p;
+        __syncthreads();
+        const uint32_t nb = min(64u, un.z - i0);
+        for (uint32_t k = 0; k < nb; ++k) {
+            const uint64_t m = sm[k];
+            const uint32_t w = word ? (uint32_t)(m >> 32) : (uint32_t)m;
+            if ((w >> bit) & 1u) {
+                if (pos < a.cap) a.list[pos] = sp[k];
+                ++pos;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -184,8 +350,17 @@ static int sm_count_bin() {
     return v > 0 ? v : 148;
 }
 
+int super_passes(uint32_t nsuper) {
+    int bits = 0;
+    while (bits < 32 && (1ull << bits) < (unsigned long long)nsuper) ++bits;
+    return (bits + 7) / 8;
+}
+
+uint64_t fine_list_offset(const Layout &L) { return L.off_ek[1 - (super_passes(L.nsuper) & 1)]; }
+
 cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStream_t st) {
     Header *hdr = header(ws);
+    const int tshift = L.tile == 8 ? 3 : (L.tile == 16 ? 4 : 5);
     BinArgs a{};
     a.hdr = hdr;
     a.list[0] = at<uint32_t>(ws, L.off_sv[0]);
@@ -196,27 +371,24 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     a.ek = at<uint32_t>(ws, L.off_ek[0]);
     a.ev = at<uint32_t>(ws, L.off_ev[0]);
     a.cap = L.cap;
-    a.tile = L.tile;
-    a.ntx = L.ntx;
+    a.nsx = (int)L.nsx;
+    a.sshift = tshift + 3;
     a.large_tiles = large_tiles;
-    a.tshift = L.tile == 8 ? 3 : (L.tile == 16 ? 4 : 5);
     k_bin_reduce<<<a.ctas, 256, 0, st>>>(a);
     k_bin_scan<<<1, 1024, 0, st>>>(a);
     k_bin_emit<<<a.ctas, 256, 0, st>>>(a);
     count_launches(3);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // Stable sort of the entries by tile id (only the bits a tile id can use).
-    int bits = 0;
-    while (bits < 32 && (1ull << bits) < (unsigned long long)L.ntiles) ++bits;
-    const int passes = (bits + 7) / 8;
+    // group the entries by super-tile (stable: render order kept inside a group)
+    const int passes = super_passes(L.nsuper);
     RadixPass p{};
     p.hist = at<uint32_t>(ws, L.off_hist);
     p.hist_stride = L.hist_ctas;
     p.htot = at<uint32_t>(ws, L.off_htot);
     p.hdr = hdr;
     p.ctas = L.ent_ctas;
-    p.n_dev = &hdr->tile_entries32;
+    p.n_dev = &hdr->super32;
     p.depth_pass = -1;
     p.skip_invalid = 0;
     for (int pass = 0; pass < passes; ++pass) {
@@ -229,10 +401,35 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
         e = launch_radix_pass(p, st);
         if (e != cudaSuccess) return e;
     }
+    const int f = passes & 1;
     const int sms = sm_count_bin();
-    k_tile_offsets<<<sms * 32, 256, 0, st>>>(hdr, at<uint32_t>(ws, L.off_ek[passes & 1]), at<uint32_t>(ws, L.off_toff),
-                                              L.ntiles);
-    count_launches(1);
+    k_group_offsets<<<sms * 8, 256, 0, st>>>(&hdr->super32, at<uint32_t>(ws, L.off_ek[f]), at<uint32_t>(ws, L.off_soff),
+                                             L.nsuper);
+    FineArgs fa{};
+    fa.hdr = hdr;
+    fa.skey = at<uint32_t>(ws, L.off_ek[f]);
+    fa.sval = at<uint32_t>(ws, L.off_ev[f]);
+    fa.soff = at<uint32_t>(ws, L.off_soff);
+    fa.ufirst = at<uint32_t>(ws, L.off_ufirst);
+    fa.units = at<uint4>(ws, L.off_units);
+    fa.ucnt = at<uint32_t>(ws, L.off_ucnt);
+    fa.toff = at<uint32_t>(ws, L.off_toff);
+    fa.list = at<uint32_t>(ws, fine_list_offset(L));
+    fa.box = at<ushort4>(ws, L.off_box);
+    fa.cap = L.cap;
+    fa.nsuper = L.nsuper;
+    fa.nsx = L.nsx;
+    fa.ntx = (uint32_t)L.ntx;
+    fa.nty = (uint32_t)L.nty;
+    fa.ntiles = L.ntiles;
+    fa.max_units = L.max_units;
+    fa.tshift = tshift;
+    k_units<<<1, 1024, 0, st>>>(fa);
+    k_fine_count<<<L.max_units, 256, 0, st>>>(fa);
+    k_fine_unit_scan<<<L.nsuper, 64, 0, st>>>(fa);
+    k_fine_offsets<<<1, 1024, 0, st>>>(fa);
+    k_fine_emit<<<L.max_units, 64, 0, st>>>(fa);
+    count_launches(6);
     return cudaGetLastError();
 }
 

@@ -35,8 +35,11 @@ struct Layout {
     uint64_t off_sk[2], off_sv[2];
     uint64_t off_part;
     uint64_t off_hist, off_htot;
-    uint64_t off_toff;
-    uint64_t off_ek[2], off_ev[2];
+    uint64_t off_toff;                 // fine-tile offsets (ntiles + 1)
+    uint64_t off_soff, off_ufirst;     // super-tile offsets (nsuper + 1), first unit of each super-tile (nsuper + 1)
+    uint64_t off_units, off_ucnt;      // units (super-tile, begin, end), per-unit counts of the 64 fine tiles
+    uint64_t off_ek[2], off_ev[2];     // super-tile entries (ping-pong); the final fine list reuses the free key buffer
+    uint32_t nsx, nsy, nsuper, max_units;
     uint64_t total;
 };
 
@@ -49,6 +52,9 @@ struct Header {
     uint32_t tile_entries32;   // min(D, cap), the count the entry sort works on
     uint32_t key_min, key_max; // over visible particles
     uint32_t sorted_buf;       // ping-pong buffer holding the ordered visible list
+    uint64_t super_entries;    // entries (particle, super-tile) (may exceed cap on overflow)
+    uint32_t super32;          // min(super_entries, cap)
+    uint32_t n_units;
     uint32_t n_species;
     uint32_t mode;
     uint32_t range_lo_enc[SPLOTCH_MAX_SPECIES];   // order-preserving encodings for atomic min/max
@@ -98,16 +104,35 @@ struct RadixPass {
     Header *hdr;
 };
 
+// Emission of (super-tile, particle) entries in render order.
 struct BinArgs {
     Header *hdr;
     const uint32_t *list[2];   // ordered visible list candidates (sorted_buf selects)
     const ushort4 *box;
     uint64_t *part;            // per-CTA partial sums
     uint32_t ctas;
-    uint32_t *ek, *ev;         // emitted entries (tile id, particle)
+    uint32_t *ek, *ev;         // emitted entries (super-tile id, particle)
     uint64_t cap;
-    int tile, ntx, tshift;     // tshift = log2(tile)
-    uint32_t large_tiles;      // particles touching more tiles than this go to the cooperative path
+    int nsx, sshift;           // super-tile columns; sshift = log2(super-tile side in pixels)
+    uint32_t large_tiles;      // particles touching more super-tiles than this are written by a whole warp
+};
+
+// Expansion of super-tile lists into fine-tile lists (64 fine tiles per super-tile).
+constexpr int kSuperSide = 8;      // fine tiles per super-tile side
+constexpr int kUnit = 4096;        // super-tile entries per unit of work
+struct FineArgs {
+    Header *hdr;
+    const uint32_t *skey, *sval;   // super-tile sorted entries
+    const uint32_t *soff;          // super-tile offsets
+    uint32_t *ufirst;              // first unit of each super-tile (nsuper + 1)
+    uint4 *units;                  // (super-tile, begin, end, 0)
+    uint32_t *ucnt;                // [unit][64]
+    uint32_t *toff;                // fine-tile offsets (ntiles + 1)
+    uint32_t *list;                // fine-tile lists
+    const ushort4 *box;
+    uint64_t cap;
+    uint32_t nsuper, nsx, ntx, nty, ntiles, max_units;
+    int tshift;
 };
 
 struct RenderArgs {
@@ -154,6 +179,8 @@ cudaError_t launch_sort(void *ws, const Layout &L, int mode, cudaStream_t st);
 cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st);
 cudaError_t launch_sort_finish(Header *hdr, cudaStream_t st);   // absorptive ordering of a depth sort
 cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStream_t st);
+int super_passes(uint32_t nsuper);             // radix passes that group entries by super-tile
+uint64_t fine_list_offset(const Layout &L);    // workspace offset of the fine-tile lists
 cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float *image, cudaStream_t st);
 cudaError_t launch_count_fragments(void *ws, const Layout &L, uint64_t *out, cudaStream_t st);
 RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, float *image);

@@ -241,13 +241,10 @@ static void launch_t(const RenderArgs &a, int ntiles, cudaStream_t st) {
 }
 
 RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, float *image) {
-    int bits = 0;
-    while (bits < 32 && (1ull << bits) < (unsigned long long)L.ntiles) ++bits;
-    const int passes = (bits + 7) / 8;
     RenderArgs a{};
     a.hdr = header(ws);
     a.toff = at<uint32_t>(ws, L.off_toff);
-    a.list = at<uint32_t>(ws, L.off_ev[passes & 1]);
+    a.list = at<uint32_t>(ws, fine_list_offset(L));
     a.geo = at<float4>(ws, L.off_geo);
     a.col = at<float4>(ws, L.off_col);
     a.image = image;

@@ -58,6 +58,14 @@ int compute_layout(uint64_t n, int width, int height, int tile, uint64_t cap, La
     L.off_hist = take((uint64_t)kRadix * L.hist_ctas * 4);
     L.off_htot = take((uint64_t)kRadix * 4);
     L.off_toff = take(((uint64_t)L.ntiles + 1) * 4);
+    L.nsx = (uint32_t)((L.ntx + kSuperSide - 1) / kSuperSide);
+    L.nsy = (uint32_t)((L.nty + kSuperSide - 1) / kSuperSide);
+    L.nsuper = L.nsx * L.nsy;
+    L.max_units = (uint32_t)((cap + kUnit - 1) / kUnit) + L.nsuper;
+    L.off_soff = take(((uint64_t)L.nsuper + 1) * 4);
+    L.off_ufirst = take(((uint64_t)L.nsuper + 1) * 4);
+    L.off_units = take((uint64_t)L.max_units * 16);
+    L.off_ucnt = take((uint64_t)L.max_units * 64 * 4);
     for (int b = 0; b < 2; ++b) {
         L.off_ek[b] = take(cap * 4 + 64);
         L.off_ev[b] = take(cap * 4 + 64);
@@ -123,12 +131,6 @@ static int read_header(const void *ws, size_t bytes, cudaStream_t st, Header *h)
     if (h->magic != kMagic) return SPLOTCH_ERR_STATE;
     if (h->layout.total > bytes) return SPLOTCH_ERR_WORKSPACE;
     return SPLOTCH_OK;
-}
-
-static int entry_passes(uint32_t ntiles) {
-    int bits = 0;
-    while (bits < 32 && (1ull << bits) < (unsigned long long)ntiles) ++bits;
-    return (bits + 7) / 8;
 }
 
 }  // namespace spl
@@ -264,7 +266,8 @@ int splotch_bin(const splotch_render_params *params, const splotch_camera *cam, 
     if ((s = check_ws(workspace, workspace_bytes, L))) return s;
     const int64_t px = params->large_threshold_px > 0 ? params->large_threshold_px
                                                        : (int64_t)(cam->width + cam->height) / 2;
-    const int64_t area = (int64_t)params->tile * params->tile;
+    const int64_t side = (int64_t)params->tile * kSuperSide;   // entries are per super-tile
+    const int64_t area = side * side;
     uint32_t large_tiles = (uint32_t)((px + area - 1) / area);
     if (large_tiles < 1) large_tiles = 1;
     return cuda_status(launch_bin(workspace, L, large_tiles, static_cast<cudaStream_t>(stream)));
@@ -428,9 +431,8 @@ int splotch_get_tile_lists(const void *workspace, size_t workspace_bytes, uint32
     if (offsets && cudaMemcpyAsync(offsets, at<uint32_t>(ws, L.off_toff), ((size_t)L.ntiles + 1) * 4,
                                    cudaMemcpyDeviceToDevice, st))
         return SPLOTCH_ERR_CUDA;
-    const int passes = entry_passes(L.ntiles);
     if (list && h.tile_entries &&
-        cudaMemcpyAsync(list, at<uint32_t>(ws, L.off_ev[passes & 1]), (size_t)h.tile_entries * 4,
+        cudaMemcpyAsync(list, at<uint32_t>(ws, fine_list_offset(L)), (size_t)h.tile_entries * 4,
                         cudaMemcpyDeviceToDevice, st))
         return SPLOTCH_ERR_CUDA;
     return SPLOTCH_OK;

@@ -17,6 +17,9 @@ __global__ void k_init_header(Header *hdr, Layout L, int n_species, int mode) {
     hdr->key_min = kInvalidKey;
     hdr->key_max = 0;
     hdr->sorted_buf = 0;
+    hdr->super_entries = 0;
+    hdr->super32 = 0;
+    hdr->n_units = 0;
     hdr->n_species = (uint32_t)n_species;
     hdr->mode = (uint32_t)mode;
     for (int s = 0; s < SPLOTCH_MAX_SPECIES; ++s) {
