@@ -3,16 +3,17 @@
 // 1. Every visible particle, in render order, adds one entry (super-tile,
 //    particle) per super-tile (8 x 8 screen tiles) its box meets; offsets come
 //    from a scan of the per-particle counts, so entries sit at fixed places.
-//    Particles touching more super-tiles than a threshold are written by a
-//    whole warp (the "split particles" idea of Section 3.2 applied to the
-//    emission of work items).
+//    The entries of particles touching more super-tiles than a threshold are
+//    shared out over the whole CTA (the "split particles" idea of Section 3.2
+//    applied to the emission of work items).
 // 2. One stable radix pass groups the entries by super-tile, keeping render
 //    order inside each group.
 // 3. Each super-tile's list is cut into units of kUnit entries.  A particle's
-//    footprint inside its super-tile is a 64-bit mask of fine tiles; per unit
-//    the fine-tile counts come from ballots, a scan over units and over fine
-//    tiles gives every (unit, fine tile) its output position, and the same
-//    ballots give each entry its rank among the earlier entries of its warp.
+//    footprint inside its super-tile is a rectangle of its 8 x 8 fine tiles;
+//    per unit the fine-tile counts come from a 2-D difference array, a scan
+//    over units and over fine tiles gives every (unit, fine tile) its output
+//    position, and one thread per fine tile then walks the unit's entries in
+//    order, appending those whose rectangle holds its tile.
 //    The result is, for every fine tile (row-major), the particles whose box
 //    meets it in render order: bit-exact, as a stable sort by tile would give.
 #include "internal.h"
@@ -80,18 +81,21 @@ __global__ void __launch_bounds__(1024) k_bin_scan(BinArgs a) {
 
 // Each CTA walks its range in steps of kBinStep particles (list order).  A
 // particle meeting at most `large_tiles` super-tiles is written by the thread
-// that owns it; the step's larger particles are split over the CTA's warps,
-// one warp per particle with its lanes across a row of super-tiles.
+// that owns it.  The cells of the step's larger particles are laid end to end
+// and dealt to all threads of the CTA, one cell per thread per round; a thread
+// finds its cell's particle by binary search over the large particles' first
+// cells, so the work is balanced whatever their sizes.
 __global__ void __launch_bounds__(256) k_bin_emit(BinArgs a) {
     constexpr int kPer = kBinStep / 256;
     __shared__ uint32_t s_p[kBinStep];        // particle index per item
     __shared__ uint32_t s_off[kBinStep];      // cells per item, then its entry offset within the step
-    __shared__ uint32_t s_lidx[kBinStep];     // items of the large particles, in list order
+    __shared__ uint32_t s_lcell[kBinStep];    // first cell of each large item among the step's large cells
+    __shared__ uint16_t s_lidx[kBinStep];     // items of the large particles, in list order
     __shared__ ushort4 s_box[kBinStep];       // super-tile box per item
+    __shared__ unsigned long long ws64[9];
     __shared__ uint32_t ws32[9];
     const uint32_t n = a.hdr->visible;
     const uint32_t *list = a.hdr->sorted_buf ? a.list[1] : a.list[0];
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t beg, end;
     bin_range(a.ctas, n, &beg, &end);
     unsigned long long running = a.part[blockIdx.x];
@@ -116,21 +120,33 @@ __global__ void __launch_bounds__(256) k_bin_emit(BinArgs a) {
         __syncthreads();
         // blocked arrangement: thread t owns items kPer*t .. kPer*t + kPer - 1
         uint32_t nt[kPer];
-        uint32_t mine = 0, mine_large = 0;
+        uint32_t mine = 0, mine_lcells = 0, mine_large = 0;
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             nt[q] = s_off[kPer * threadIdx.x + q];
             mine += nt[q];
-            mine_large += nt[q] > a.large_tiles;
+            if (nt[q] > a.large_tiles) {
+                mine_lcells += nt[q];
+                ++mine_large;
+            }
         }
-        uint32_t tot, ltot;
-        uint32_t off = block_exclusive_scan<256>(mine, ws32, &tot);
+        unsigned long long tot2;
+        const unsigned long long pre2 =
+            block_exclusive_scan64<256>((unsigned long long)mine | ((unsigned long long)mine_lcells << 32), ws64, &tot2);
+        uint32_t ltot;
         uint32_t lpos = block_exclusive_scan<256>(mine_large, ws32, &ltot);
+        const uint32_t tot = (uint32_t)tot2, lctot = (uint32_t)(tot2 >> 32);
+        uint32_t off = (uint32_t)pre2, lcell = (uint32_t)(pre2 >> 32);
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const uint32_t j = kPer * threadIdx.x + q;
             s_off[j] = off;
-            if (nt[q] > a.large_tiles) s_lidx[lpos++] = j;
+            if (nt[q] > a.large_tiles) {
+                s_lidx[lpos] = (uint16_t)j;
+                s_lcell[lpos] = lcell;
+                ++lpos;
+                lcell += nt[q];
+            }
             off += nt[q];
         }
         __syncthreads();
@@ -149,21 +165,24 @@ __global__ void __launch_bounds__(256) k_bin_emit(BinArgs a) {
                         a.ev[e] = p;
                     }
         }
-        // large particles: one warp per particle, lanes across a row
-        for (uint32_t i = warp; i < ltot; i += 8) {
-            const uint32_t j = s_lidx[i];
-            const uint32_t p = s_p[j];
+        // large particles: their cells dealt over the CTA
+        for (uint32_t c = threadIdx.x; c < lctot; c += 256) {
+            uint32_t lo = 0, hi = ltot;       // last i with s_lcell[i] <= c
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (s_lcell[mid] <= c) lo = mid;
+                else hi = mid;
+            }
+            const uint32_t j = s_lidx[lo];
+            const uint32_t k = c - s_lcell[lo];
             const ushort4 b = s_box[j];
             const uint32_t w = (uint32_t)(b.z - b.x + 1);
-            unsigned long long e0 = running + s_off[j];
-            for (int ty = b.y; ty <= b.w; ++ty, e0 += w)
-                for (uint32_t c = lane; c < w; c += 32) {
-                    const unsigned long long e = e0 + c;
-                    if (e < a.cap) {
-                        a.ek[e] = (uint32_t)(ty * a.nsx + b.x) + c;
-                        a.ev[e] = p;
-                    }
-                }
+            const uint32_t row = k / w, col = k - row * w;
+            const unsigned long long e = running + s_off[j] + k;
+            if (e < a.cap) {
+                a.ek[e] = (uint32_t)((b.y + row) * a.nsx + b.x + col);
+                a.ev[e] = s_p[j];
+            }
         }
         nlarge_cta += ltot;
         running += tot;
@@ -191,23 +210,31 @@ __global__ void __launch_bounds__(256) k_group_offsets(const uint32_t *count, co
     }
 }
 
-// Fine tiles of super-tile s that a particle's pixel box meets, as a 64-bit
-// mask: bit 8 r + c for row r and column c inside the super-tile.
-__device__ __forceinline__ uint64_t fine_mask(const ushort4 b, int tshift, uint32_t s, uint32_t nsx) {
-    const int ox = (int)(s % nsx) * kSuperSide, oy = (int)(s / nsx) * kSuperSide;
-    const int c0 = max((b.x >> tshift) - ox, 0), c1 = min((b.z >> tshift) - ox, kSuperSide - 1);
-    const int r0 = max((b.y >> tshift) - oy, 0), r1 = min((b.w >> tshift) - oy, kSuperSide - 1);
-    if (c0 > c1 || r0 > r1) return 0ull;
-    const uint64_t row = (0xFFull >> (kSuperSide - 1 - c1)) & (0xFFull << c0);
-    uint64_t m = 0;
-    for (int r = r0; r <= r1; ++r) m |= row << (kSuperSide * r);
-    return m;
+// Fine-tile rectangle (columns c0..c1, rows r0..r1, in 0..7) that a
+// particle's pixel box meets inside the super-tile whose first fine tile is
+// (ox, oy).
+struct FineRect {
+    int c0, c1, r0, r1;
+};
+__device__ __forceinline__ FineRect fine_rect(const ushort4 b, int tshift, int ox, int oy) {
+    FineRect f;
+    f.c0 = max((b.x >> tshift) - ox, 0);
+    f.c1 = min((b.z >> tshift) - ox, kSuperSide - 1);
+    f.r0 = max((b.y >> tshift) - oy, 0);
+    f.r1 = min((b.w >> tshift) - oy, kSuperSide - 1);
+    return f;
 }
 
-__device__ __forceinline__ uint64_t warp_or64(uint64_t m) {
-    const uint32_t lo = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)m);
-    const uint32_t hi = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)(m >> 32));
-    return ((uint64_t)hi << 32) | lo;
+// The same rectangle as a 64-bit mask: bit 8 r + c.
+__device__ __forceinline__ uint64_t fine_mask(const FineRect f) {
+    if (f.c0 > f.c1 || f.r0 > f.r1) return 0ull;
+    const uint64_t row = (0xFFull >> (kSuperSide - 1 - f.c1)) & (0xFFull << f.c0);
+    const uint64_t rows = (0xFFull >> (kSuperSide - 1 - f.r1)) & (0xFFull << f.r0);
+    // spread the 8 row bits to bytes (bit r -> bit 8 r), then replicate the column pattern
+    uint64_t spread = 0;
+#pragma unroll
+    for (int r = 0; r < kSuperSide; ++r) spread |= ((rows >> r) & 1ull) << (kSuperSide * r);
+    return spread * row;
 }
 
 // Cut every super-tile's list into units of at most kUnit entries.
@@ -239,23 +266,31 @@ __global__ void __launch_bounds__(1024) k_units(FineArgs a) {
 }
 
 // Per unit: how many of the unit's entries meet each of the super-tile's 64
-// fine tiles.
+// fine tiles, accumulated as a 2-D difference array (four updates per entry)
+// and summed at the end.
 __global__ void __launch_bounds__(256) k_fine_count(FineArgs a) {
-    __shared__ uint32_t cnt[64];
+    __shared__ int diff[kSuperSide + 1][kSuperSide + 1];
     const uint32_t u = blockIdx.x;
     if (u >= a.hdr->n_units) return;
     const uint4 un = a.units[u];
-    if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+    const int ox = (int)(un.x % a.nsx) * kSuperSide, oy = (int)(un.x / a.nsx) * kSuperSide;
+    if (threadIdx.x < (kSuperSide + 1) * (kSuperSide + 1)) (&diff[0][0])[threadIdx.x] = 0;
     __syncthreads();
     for (uint32_t i = un.y + threadIdx.x; i < un.z; i += 256) {
-        uint64_t m = fine_mask(a.box[a.sval[i]], a.tshift, un.x, a.nsx);
-        while (m) {
-            atomicAdd(&cnt[__ffsll((long long)m) - 1], 1u);
-            m &= m - 1;
-        }
+        const FineRect f = fine_rect(a.box[a.sval[i]], a.tshift, ox, oy);
+        atomicAdd(&diff[f.r0][f.c0], 1);
+        atomicAdd(&diff[f.r0][f.c1 + 1], -1);
+        atomicAdd(&diff[f.r1 + 1][f.c0], -1);
+        atomicAdd(&diff[f.r1 + 1][f.c1 + 1], 1);
     }
     __syncthreads();
-    if (threadIdx.x < 64) a.ucnt[(size_t)u * 64 + threadIdx.x] = cnt[threadIdx.x];
+    if (threadIdx.x < 64) {
+        const int r = threadIdx.x / kSuperSide, c = threadIdx.x % kSuperSide;
+        int v = 0;
+        for (int rr = 0; rr <= r; ++rr)
+            for (int cc = 0; cc <= c; ++cc) v += diff[rr][cc];
+        a.ucnt[(size_t)u * 64 + threadIdx.x] = (uint32_t)v;
+    }
 }
 
 // Per super-tile: each fine tile's running count over the super-tile's units
@@ -309,32 +344,43 @@ __global__ void __launch_bounds__(1024) k_fine_offsets(FineArgs a) {
 }
 
 // Per unit, one thread per fine tile: walk the unit's entries in order
-// (64 at a time: each thread stages one entry's particle and fine-tile mask
-// in shared memory, read back by broadcast) and append the
-// particle of every entry whose mask has the thread's tile, starting at the
-// tile's offset plus the unit's offset within the tile.  Render order is kept
-// because each tile's entries are appended in list order by one thread.
+// (256 at a time: each thread stages four entries' particles and fine-tile
+// masks in shared memory, read back by broadcast) and append the particle of
+// every entry whose mask has the thread's tile, starting at the tile's offset
+// plus the unit's offset within the tile.  Render order is kept because each
+// tile's entries are appended in list order by one thread.
 __global__ void __launch_bounds__(64) k_fine_emit(FineArgs a) {
-    __shared__ uint64_t sm[64];
-    __shared__ uint32_t sp[64];
+    constexpr int kStage = 256;
+    __shared__ uint2 sm[kStage];     // mask as two words
+    __shared__ uint32_t sp[kStage];
     const uint32_t u = blockIdx.x;
     if (u >= a.hdr->n_units) return;
     const uint4 un = a.units[u];
     const uint32_t s = un.x, t = threadIdx.x;
-    const uint32_t tx = (s % a.nsx) * kSuperSide + (t % kSuperSide), ty = (s / a.nsx) * kSuperSide + t / kSuperSide;
+    const int ox = (int)(s % a.nsx) * kSuperSide, oy = (int)(s / a.nsx) * kSuperSide;
+    const uint32_t tx = (uint32_t)ox + (t % kSuperSide), ty = (uint32_t)oy + t / kSuperSide;
     uint64_t pos = (tx < a.ntx && ty < a.nty) ? (uint64_t)a.toff[ty * a.ntx + tx] + a.ucnt[(size_t)u * 64 + t] : 0;
     const uint32_t word = t >> 5, bit = t & 31;
-    for (uint32_t i0 = un.y; i0 < un.z; i0 += 64) {
-        const uint32_t i = i0 + t;
-        const uint32_t p = i < un.z ? a.sval[i] : 0u;
-        sm[t] = i < un.z ? fine_mask(a.box[p], a.tshift, s, a.nsx) : 0ull;
-        sp[t] = p;
+    for (uint32_t i0 = un.y; i0 < un.z; i0 += kStage) {
+        uint32_t pv[kStage / 64];
+#pragma unroll
+        for (int q = 0; q < kStage / 64; ++q) {
+            const uint32_t i = i0 + q * 64 + t;
+            pv[q] = i < un.z ? a.sval[i] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < kStage / 64; ++q) {
+            const uint32_t i = i0 + q * 64 + t;
+            const uint64_t m = i < un.z ? fine_mask(fine_rect(a.box[pv[q]], a.tshift, ox, oy)) : 0ull;
+            sm[q * 64 + t] = make_uint2((uint32_t)m, (uint32_t)(m >> 32));
+            sp[q * 64 + t] = pv[q];
+        }
         __syncthreads();
-        const uint32_t nb = min(64u, un.z - i0);
+        const uint32_t nb = min((uint32_t)kStage, un.z - i0);
+#pragma unroll 4
         for (uint32_t k = 0; k < nb; ++k) {
-            const uint64_t m = sm[k];
-            const uint32_t w = word ? (uint32_t)(m >> 32) : (uint32_t)m;
-            if ((w >> bit) & 1u) {
+            const uint2 m = sm[k];
+            if ((((word ? m.y : m.x) >> bit) & 1u)) {
                 if (pos < a.cap) a.list[pos] = sp[k];
                 ++pos;
             }
