@@ -12,8 +12,8 @@
 //    footprint inside its super-tile is a rectangle of its 8 x 8 fine tiles;
 //    per unit the fine-tile counts come from a 2-D difference array, a scan
 //    over units and over fine tiles gives every (unit, fine tile) its output
-//    position, and one thread per fine tile then walks the unit's entries in
-//    order, appending those whose rectangle holds its tile.
+//    position, and row and column ballots over each warp's entries give every
+//    (entry, fine tile) its rank inside the tile.
 //    The result is, for every fine tile (row-major), the particles whose box
 //    meets it in render order: bit-exact, as a stable sort by tile would give.
 #include "internal.h"
@@ -79,109 +79,126 @@ __global__ void __launch_bounds__(1024) k_bin_scan(BinArgs a) {
     }
 }
 
-// Each CTA walks its range in steps of kBinStep particles (list order).  A
-// particle meeting at most `large_tiles` super-tiles is written by the thread
-// that owns it.  The cells of the step's larger particles are laid end to end
-// and dealt to all threads of the CTA, one cell per thread per round; a thread
-// finds its cell's particle by binary search over the large particles' first
-// cells, so the work is balanced whatever their sizes.
-__global__ void __launch_bounds__(256) k_bin_emit(BinArgs a) {
-    constexpr int kPer = kBinStep / 256;
-    __shared__ uint32_t s_p[kBinStep];        // particle index per item
-    __shared__ uint32_t s_off[kBinStep];      // cells per item, then its entry offset within the step
-    __shared__ uint32_t s_lcell[kBinStep];    // first cell of each large item among the step's large cells
-    __shared__ uint16_t s_lidx[kBinStep];     // items of the large particles, in list order
-    __shared__ ushort4 s_box[kBinStep];       // super-tile box per item
-    __shared__ unsigned long long ws64[9];
-    __shared__ uint32_t ws32[9];
+// Each CTA walks its range in steps of kBinStep particles (list order); warp
+// w takes the step's w-th run of 256 particles, 32 at a time, and keeps them in
+// registers.  Warp scans give each particle its first entry within the warp's
+// run, a scan of the 8 warp totals places the runs.  A particle meeting at
+// most `large_tiles` super-tiles is written by its own lane.  The larger ones
+// go to the warp's segment of shared memory; their cells are laid end to end
+// (warp by warp, list order) and dealt to all threads of the CTA, one cell per
+// thread per round.  A thread finds its cell's warp from the warp totals and
+// its particle by binary search over the segment's first cells, so the work
+// is balanced whatever the particles' sizes.
+__global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
+    constexpr int kRounds = kBinStep / 256;
+    __shared__ uint32_t s_lp[kBinStep];       // large particles, per warp segment of 256, in list order
+    __shared__ uint32_t s_loff[kBinStep];     // their first entry within the warp's run
+    __shared__ uint32_t s_lcell[kBinStep];    // their first cell among the warp's large cells
+    __shared__ ushort4 s_lbox[kBinStep];      // their super-tile boxes
+    __shared__ uint32_t s_wtot[3][8];         // per warp: cells, large particles, large cells
     const uint32_t n = a.hdr->visible;
     const uint32_t *list = a.hdr->sorted_buf ? a.list[1] : a.list[0];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
     uint64_t beg, end;
     bin_range(a.ctas, n, &beg, &end);
     unsigned long long running = a.part[blockIdx.x];
     uint32_t nlarge_cta = 0;
     for (uint64_t step = beg; step < end; step += kBinStep) {
         const uint32_t m = (uint32_t)min((uint64_t)kBinStep, end - step);
+        uint32_t p[kRounds], off[kRounds];
+        ushort4 tb[kRounds];
+        uint32_t cells = 0, nl = 0, lcells = 0;
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const uint32_t j = threadIdx.x + 256u * q;
-            uint32_t p = 0, nt = 0;
-            ushort4 tb = make_ushort4(1, 1, 0, 0);
+        for (int q = 0; q < kRounds; ++q) {
+            const uint32_t j = warp * 256u + 32u * q + lane;
+            uint32_t nt = 0;
+            p[q] = 0;
+            tb[q] = make_ushort4(1, 1, 0, 0);
             if (j < m) {
-                p = list[step + j];
-                const ushort4 b = a.box[p];
-                tb = make_ushort4(b.x >> a.sshift, b.y >> a.sshift, b.z >> a.sshift, b.w >> a.sshift);
-                nt = (uint32_t)(tb.z - tb.x + 1) * (uint32_t)(tb.w - tb.y + 1);
+                p[q] = list[step + j];
+                const ushort4 b = a.box[p[q]];
+                tb[q] = make_ushort4(b.x >> a.sshift, b.y >> a.sshift, b.z >> a.sshift, b.w >> a.sshift);
+                nt = (uint32_t)(tb[q].z - tb[q].x + 1) * (uint32_t)(tb[q].w - tb[q].y + 1);
             }
-            s_p[j] = p;
-            s_off[j] = nt;
-            s_box[j] = tb;
+            const bool big = nt > a.large_tiles;
+            const uint32_t inc = warp_inclusive_scan(nt);
+            const uint32_t linc = warp_inclusive_scan(big ? nt : 0u);
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, big);
+            off[q] = cells + inc - nt;
+            if (big) {
+                const uint32_t r = warp * 256u + nl + __popc(bal & lt);
+                s_lp[r] = p[q];
+                s_loff[r] = off[q];
+                s_lcell[r] = lcells + linc - nt;
+                s_lbox[r] = tb[q];
+                tb[q] = make_ushort4(1, 1, 0, 0);    // nothing left for the lane to write
+            }
+            cells += __shfl_sync(0xFFFFFFFFu, inc, 31);
+            lcells += __shfl_sync(0xFFFFFFFFu, linc, 31);
+            nl += __popc(bal);
+        }
+        if (lane == 0) {
+            s_wtot[0][warp] = cells;
+            s_wtot[1][warp] = nl;
+            s_wtot[2][warp] = lcells;
         }
         __syncthreads();
-        // blocked arrangement: thread t owns items kPer*t .. kPer*t + kPer - 1
-        uint32_t nt[kPer];
-        uint32_t mine = 0, mine_lcells = 0, mine_large = 0;
+        uint32_t wc[8], wl[8], wlc[8];
+        uint32_t tot = 0, ltot = 0, lctot = 0;
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            nt[q] = s_off[kPer * threadIdx.x + q];
-            mine += nt[q];
-            if (nt[q] > a.large_tiles) {
-                mine_lcells += nt[q];
-                ++mine_large;
-            }
+        for (int w = 0; w < 8; ++w) {
+            wc[w] = tot;
+            wl[w] = s_wtot[1][w];
+            wlc[w] = lctot;
+            tot += s_wtot[0][w];
+            ltot += wl[w];
+            lctot += s_wtot[2][w];
         }
-        unsigned long long tot2;
-        const unsigned long long pre2 =
-            block_exclusive_scan64<256>((unsigned long long)mine | ((unsigned long long)mine_lcells << 32), ws64, &tot2);
-        uint32_t ltot;
-        uint32_t lpos = block_exclusive_scan<256>(mine_large, ws32, &ltot);
-        const uint32_t tot = (uint32_t)tot2, lctot = (uint32_t)(tot2 >> 32);
-        uint32_t off = (uint32_t)pre2, lcell = (uint32_t)(pre2 >> 32);
+        uint32_t base = 0;
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const uint32_t j = kPer * threadIdx.x + q;
-            s_off[j] = off;
-            if (nt[q] > a.large_tiles) {
-                s_lidx[lpos] = (uint16_t)j;
-                s_lcell[lpos] = lcell;
-                ++lpos;
-                lcell += nt[q];
-            }
-            off += nt[q];
-        }
-        __syncthreads();
+        for (int w = 0; w < 8; ++w)
+            if ((uint32_t)w == warp) base = wc[w];
         // small particles: the owner writes its entries
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const uint32_t j = kPer * threadIdx.x + q;
-            if (nt[q] == 0 || nt[q] > a.large_tiles) continue;
-            const uint32_t p = s_p[j];
-            const ushort4 b = s_box[j];
-            unsigned long long e = running + s_off[j];
+        for (int q = 0; q < kRounds; ++q) {
+            const ushort4 b = tb[q];
+            unsigned long long e = running + base + off[q];
             for (int ty = b.y; ty <= b.w; ++ty)
                 for (int tx = b.x; tx <= b.z; ++tx, ++e)
                     if (e < a.cap) {
                         a.ek[e] = (uint32_t)(ty * a.nsx + tx);
-                        a.ev[e] = p;
+                        a.ev[e] = p[q];
                     }
         }
         // large particles: their cells dealt over the CTA
         for (uint32_t c = threadIdx.x; c < lctot; c += 256) {
-            uint32_t lo = 0, hi = ltot;       // last i with s_lcell[i] <= c
+            uint32_t seg = 0, segn = wl[0], cbase = wc[0], lbase = wlc[0];
+#pragma unroll
+            for (int w = 1; w < 8; ++w)
+                if (wlc[w] <= c) {
+                    seg = w;
+                    segn = wl[w];
+                    cbase = wc[w];
+                    lbase = wlc[w];
+                }
+            const uint32_t cl = c - lbase;
+            const uint32_t *lc = s_lcell + seg * 256u;
+            uint32_t lo = 0, hi = segn;       // last i with lc[i] <= cl
             while (hi - lo > 1) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (s_lcell[mid] <= c) lo = mid;
+                if (lc[mid] <= cl) lo = mid;
                 else hi = mid;
             }
-            const uint32_t j = s_lidx[lo];
-            const uint32_t k = c - s_lcell[lo];
-            const ushort4 b = s_box[j];
+            const uint32_t i = seg * 256u + lo;
+            const uint32_t k = cl - lc[lo];
+            const ushort4 b = s_lbox[i];
             const uint32_t w = (uint32_t)(b.z - b.x + 1);
             const uint32_t row = k / w, col = k - row * w;
-            const unsigned long long e = running + s_off[j] + k;
+            const unsigned long long e = running + cbase + s_loff[i] + k;
             if (e < a.cap) {
                 a.ek[e] = (uint32_t)((b.y + row) * a.nsx + b.x + col);
-                a.ev[e] = s_p[j];
+                a.ev[e] = s_lp[i];
             }
         }
         nlarge_cta += ltot;
@@ -223,18 +240,6 @@ __device__ __forceinline__ FineRect fine_rect(const ushort4 b, int tshift, int o
     f.r0 = max((b.y >> tshift) - oy, 0);
     f.r1 = min((b.w >> tshift) - oy, kSuperSide - 1);
     return f;
-}
-
-// The same rectangle as a 64-bit mask: bit 8 r + c.
-__device__ __forceinline__ uint64_t fine_mask(const FineRect f) {
-    if (f.c0 > f.c1 || f.r0 > f.r1) return 0ull;
-    const uint64_t row = (0xFFull >> (kSuperSide - 1 - f.c1)) & (0xFFull << f.c0);
-    const uint64_t rows = (0xFFull >> (kSuperSide - 1 - f.r1)) & (0xFFull << f.r0);
-    // spread the 8 row bits to bytes (bit r -> bit 8 r), then replicate the column pattern
-    uint64_t spread = 0;
-#pragma unroll
-    for (int r = 0; r < kSuperSide; ++r) spread |= ((rows >> r) & 1ull) << (kSuperSide * r);
-    return spread * row;
 }
 
 // Cut every super-tile's list into units of at most kUnit entries.
@@ -343,49 +348,150 @@ __global__ void __launch_bounds__(1024) k_fine_offsets(FineArgs a) {
     }
 }
 
-// Per unit, one thread per fine tile: walk the unit's entries in order
-// (256 at a time: each thread stages four entries' particles and fine-tile
-// masks in shared memory, read back by broadcast) and append the particle of
-// every entry whose mask has the thread's tile, starting at the tile's offset
-// plus the unit's offset within the tile.  Render order is kept because each
-// tile's entries are appended in list order by one thread.
-__global__ void __launch_bounds__(64) k_fine_emit(FineArgs a) {
-    constexpr int kStage = 256;
-    __shared__ uint2 sm[kStage];     // mask as two words
-    __shared__ uint32_t sp[kStage];
+// Fine entries of one unit staged in shared memory (tile by tile) before they
+// are written out; units with more go straight to global memory.
+constexpr int kFineBuf = 8192;
+
+// Per unit, 256 entries at a time, one entry per thread.  A warp's 32
+// entries (list order = lane order) are described by 16 ballots: for each
+// fine-tile row r, the lanes whose rectangle spans r, and for each column c,
+// the lanes whose rectangle spans c; the lanes meeting fine tile (r, c) are
+// the AND of the two.  A lane's place in tile (r, c) is the number of earlier
+// lanes meeting it, after the earlier warps' and earlier chunks' entries
+// (a scan over the 8 warps per tile).  The warp's (entry, fine tile) pairs are
+// laid end to end and dealt over its lanes, so the work follows the number of
+// fine entries whatever the entries' sizes, and render order is kept inside
+// every tile.  The unit's
+// entries of a tile form one run of the tile's list; the runs are gathered in
+// shared memory and copied out whole, so the global writes are coalesced.
+__global__ void __launch_bounds__(256) k_fine_emit(FineArgs a) {
+    __shared__ uint32_t s_buf[kFineBuf];
+    __shared__ __align__(16) uint32_t s_b[8][16];   // per warp: row ballots 0..7, column ballots 8..15
+    __shared__ uint32_t s_wcnt[8][64];              // per warp: its entries meeting each fine tile
+    __shared__ uint32_t s_pos[8][64];               // per warp: its first place in each fine tile's run
+    __shared__ uint32_t s_run[64];                  // entries placed so far per fine tile
+    __shared__ uint32_t s_lb[65];                   // start of each fine tile's run in s_buf
+    __shared__ unsigned long long s_gbase[64];      // list position of each fine tile's run
+    __shared__ uint32_t s_pstart[8][32];            // per warp and lane: first (entry, tile) pair of the entry
+    __shared__ uint32_t s_pinfo[8][32];             // per warp and lane: first column, first row, width, 2^16/width + 1
+    __shared__ uint32_t s_pp[8][32];                // per warp and lane: the entry's particle
     const uint32_t u = blockIdx.x;
-    if (u >= a.hdr->n_units) return;
+    const uint32_t n_units = a.hdr->n_units;
+    if (u >= n_units) return;
     const uint4 un = a.units[u];
-    const uint32_t s = un.x, t = threadIdx.x;
+    const uint32_t s = un.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ox = (int)(s % a.nsx) * kSuperSide, oy = (int)(s / a.nsx) * kSuperSide;
-    const uint32_t tx = (uint32_t)ox + (t % kSuperSide), ty = (uint32_t)oy + t / kSuperSide;
-    uint64_t pos = (tx < a.ntx && ty < a.nty) ? (uint64_t)a.toff[ty * a.ntx + tx] + a.ucnt[(size_t)u * 64 + t] : 0;
-    const uint32_t word = t >> 5, bit = t & 31;
-    for (uint32_t i0 = un.y; i0 < un.z; i0 += kStage) {
-        uint32_t pv[kStage / 64];
+    if (warp == 0) {
+        // this unit's count per fine tile: up to the next unit of the same super-tile, or the tile's total
+        const bool last = u + 1 >= n_units || a.units[u + 1].x != s;
+        uint32_t cnt[2];
 #pragma unroll
-        for (int q = 0; q < kStage / 64; ++q) {
-            const uint32_t i = i0 + q * 64 + t;
-            pv[q] = i < un.z ? a.sval[i] : 0u;
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t t = lane + 32u * h;
+            const uint32_t tx = (uint32_t)ox + (t % kSuperSide), ty = (uint32_t)oy + t / kSuperSide;
+            cnt[h] = 0;
+            unsigned long long g = 0;
+            if (tx < a.ntx && ty < a.nty) {
+                const uint32_t tile = ty * a.ntx + tx;
+                const uint32_t here = a.ucnt[(size_t)u * 64 + t];
+                const uint32_t next = last ? a.toff[tile + 1] - a.toff[tile] : a.ucnt[(size_t)(u + 1) * 64 + t];
+                g = (unsigned long long)a.toff[tile] + here;
+                cnt[h] = next > here ? next - here : 0u;
+            }
+            s_gbase[t] = g;
+            s_run[t] = 0;
         }
+        const uint32_t i0 = warp_inclusive_scan(cnt[0]);
+        const uint32_t tot0 = __shfl_sync(0xFFFFFFFFu, i0, 31);
+        const uint32_t i1 = warp_inclusive_scan(cnt[1]);
+        s_lb[lane] = i0 - cnt[0];
+        s_lb[lane + 32] = tot0 + i1 - cnt[1];
+        if (lane == 31) s_lb[64] = tot0 + i1;
+    }
+    __syncthreads();
+    const bool staged = s_lb[64] <= (uint32_t)kFineBuf;
+    for (uint32_t i0 = un.y; i0 < un.z; i0 += 256) {
+        const uint32_t i = i0 + threadIdx.x;
+        uint32_t p = 0;
+        FineRect f{1, 0, 1, 0};                      // empty
+        if (i < un.z) {
+            p = a.sval[i];
+            f = fine_rect(a.box[p], a.tshift, ox, oy);
+        }
+        const uint32_t rows = f.r0 <= f.r1 ? (0xFFu >> (kSuperSide - 1 - f.r1)) & (0xFFu << f.r0) : 0u;
+        const uint32_t cols = f.c0 <= f.c1 ? (0xFFu >> (kSuperSide - 1 - f.c1)) & (0xFFu << f.c0) : 0u;
+        uint32_t b[16];
 #pragma unroll
-        for (int q = 0; q < kStage / 64; ++q) {
-            const uint32_t i = i0 + q * 64 + t;
-            const uint64_t m = i < un.z ? fine_mask(fine_rect(a.box[pv[q]], a.tshift, ox, oy)) : 0ull;
-            sm[q * 64 + t] = make_uint2((uint32_t)m, (uint32_t)(m >> 32));
-            sp[q * 64 + t] = pv[q];
+        for (int k = 0; k < kSuperSide; ++k) {
+            b[k] = __ballot_sync(0xFFFFFFFFu, (rows >> k) & 1u);
+            b[kSuperSide + k] = __ballot_sync(0xFFFFFFFFu, (cols >> k) & 1u);
+        }
+        if (lane == 0) {
+            uint4 *d = reinterpret_cast<uint4 *>(s_b[warp]);
+            d[0] = make_uint4(b[0], b[1], b[2], b[3]);
+            d[1] = make_uint4(b[4], b[5], b[6], b[7]);
+            d[2] = make_uint4(b[8], b[9], b[10], b[11]);
+            d[3] = make_uint4(b[12], b[13], b[14], b[15]);
+        }
+        __syncwarp();
+        {
+            const uint32_t bc = s_b[warp][kSuperSide + (lane & 7)];
+            s_wcnt[warp][lane] = __popc(s_b[warp][lane >> 3] & bc);
+            s_wcnt[warp][lane + 32] = __popc(s_b[warp][(lane >> 3) + 4] & bc);
         }
         __syncthreads();
-        const uint32_t nb = min((uint32_t)kStage, un.z - i0);
-#pragma unroll 4
-        for (uint32_t k = 0; k < nb; ++k) {
-            const uint2 m = sm[k];
-            if ((((word ? m.y : m.x) >> bit) & 1u)) {
-                if (pos < a.cap) a.list[pos] = sp[k];
-                ++pos;
+        if (threadIdx.x < 64) {
+            const uint32_t t = threadIdx.x;
+            uint32_t run = s_run[t];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                s_pos[w][t] = run;
+                run += s_wcnt[w][t];
+            }
+            s_run[t] = run;
+        }
+        __syncthreads();
+        // (entry, fine tile) pairs of the warp, entry by entry, dealt over the lanes
+        const uint32_t w = f.c1 - f.c0 + 1, h = f.r1 - f.r0 + 1;
+        const uint32_t npair = f.c0 <= f.c1 && f.r0 <= f.r1 ? w * h : 0u;
+        const uint32_t pinc = warp_inclusive_scan(npair);
+        const uint32_t K = __shfl_sync(0xFFFFFFFFu, pinc, 31);
+        s_pstart[warp][lane] = pinc - npair;
+        s_pinfo[warp][lane] = (uint32_t)f.c0 | ((uint32_t)f.r0 << 3) | (w << 6) | ((w ? 65536u / w + 1u : 0u) << 10);
+        s_pp[warp][lane] = p;
+        __syncwarp();
+        for (uint32_t q0 = 0; q0 < K; q0 += 32) {
+            const uint32_t q = q0 + lane;
+            if (q < K) {
+                uint32_t o = 0;                  // last lane whose pairs start at or before q
+#pragma unroll
+                for (uint32_t d = 16; d > 0; d >>= 1)
+                    if (s_pstart[warp][o + d] <= q) o += d;
+                const uint32_t k = q - s_pstart[warp][o];
+                const uint32_t info = s_pinfo[warp][o];
+                const uint32_t ow = (info >> 6) & 15u;
+                const uint32_t rr = (k * (info >> 10)) >> 16, cc = k - rr * ow;
+                const uint32_t r = (info >> 3 & 7u) + rr, c = (info & 7u) + cc;
+                const uint32_t t = r * kSuperSide + c;
+                const uint32_t kk = s_pos[warp][t] + __popc(s_b[warp][r] & s_b[warp][kSuperSide + c] & ((1u << o) - 1u));
+                const uint32_t pp = s_pp[warp][o];
+                if (staged) {
+                    const uint32_t qq = s_lb[t] + kk;
+                    if (qq < (uint32_t)kFineBuf) s_buf[qq] = pp;
+                } else {
+                    const unsigned long long pos = s_gbase[t] + kk;
+                    if (pos < a.cap) a.list[pos] = pp;
+                }
             }
         }
-        __syncthreads();
+    }
+    if (!staged) return;
+    __syncthreads();
+    for (int t = warp; t < 64; t += 8) {
+        const uint32_t b0 = s_lb[t], n = s_lb[t + 1] - b0;
+        const unsigned long long g = s_gbase[t];
+        for (uint32_t k = lane; k < n; k += 32)
+            if (g + k < a.cap) a.list[g + k] = s_buf[b0 + k];
     }
 }
 
@@ -474,7 +580,7 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     k_fine_count<<<L.max_units, 256, 0, st>>>(fa);
     k_fine_unit_scan<<<L.nsuper, 64, 0, st>>>(fa);
     k_fine_offsets<<<1, 1024, 0, st>>>(fa);
-    k_fine_emit<<<L.max_units, 64, 0, st>>>(fa);
+    k_fine_emit<<<L.max_units, 256, 0, st>>>(fa);
     count_launches(6);
     return cudaGetLastError();
 }

@@ -57,6 +57,7 @@ struct Header {
     uint32_t n_units;
     uint32_t n_species;
     uint32_t mode;
+    uint32_t series_only;      // every species with particles has A <= kSeriesMaxA
     uint32_t range_lo_enc[SPLOTCH_MAX_SPECIES];   // order-preserving encodings for atomic min/max
     uint32_t range_hi_enc[SPLOTCH_MAX_SPECIES];
     float lo[SPLOTCH_MAX_SPECIES], hi[SPLOTCH_MAX_SPECIES];
@@ -64,6 +65,10 @@ struct Header {
 };
 
 constexpr uint64_t kHeaderBytes = 4096;
+
+// Absorption up to which the renderer takes a layer's source and transmission
+// from a series in A g instead of an exponential.
+constexpr float kSeriesMaxA = 0.125f;
 static_assert(sizeof(Header) <= kHeaderBytes, "header too large");
 
 // Transform parameters in the form the kernels use (host computes once).
@@ -119,7 +124,7 @@ struct BinArgs {
 
 // Expansion of super-tile lists into fine-tile lists (64 fine tiles per super-tile).
 constexpr int kSuperSide = 8;      // fine tiles per super-tile side
-constexpr int kUnit = 4096;        // super-tile entries per unit of work
+constexpr int kUnit = 2048;        // super-tile entries per unit of work
 struct FineArgs {
     Header *hdr;
     const uint32_t *skey, *sval;   // super-tile sorted entries

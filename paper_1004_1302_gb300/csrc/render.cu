@@ -21,15 +21,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
 // An absorbing layer with A <= kSeriesMaxA takes its source and
@@ -37,9 +28,8 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 //   q = (1 - e^{-y})/y = 1 + yn/2 + yn^2/6 + yn^3/24 + ...
 // truncated after yn^3 (relative error below y^4/5! < 2.1e-6 for y <= 1/8),
 // S = E g q and T = 1 + yn q, with no cancellation; A = 0 gives q = 1, T = 1.
-// Larger A takes T from exp2 and S = E (1 - T)/A.
-constexpr float kSeriesMaxA = 0.125f;
-
+// With u = T_acc g q the update is C += E u, T_acc -= A u.  Larger A takes T
+// from exp2 and S = E (1 - T)/A.
 __device__ __forceinline__ float2 q_series(float2 yn) {
     float2 q = f2(1.0f / 24.0f);
     q = __ffma2_rn(q, yn, f2(1.0f / 6.0f));
@@ -59,7 +49,8 @@ template <int B> struct RenderSmem {
 };
 
 // One screen tile, rendered by the whole CTA (all threads must call it).
-template <int T, int MODE, int B>
+// SERIES: every particle's A is at most kSeriesMaxA (absorptive mode).
+template <int T, int MODE, int B, bool SERIES>
 __device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile, RenderSmem<B> &sm) {
     constexpr int kThreads = T * T / 2;
     constexpr int WX = 8, WY = 8;               // pixel block of one warp (two pixels per lane)
@@ -137,11 +128,10 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile,
                 keep = ddx * ddx + ddy * ddy <= g.z * 1.0001f + 0.01f;
             }
             uint32_t mask = __ballot_sync(0xFFFFFFFFu, keep);
-            while (mask) {
-                const int j = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const float4 p0 = s0[buf][c + j], p1 = s1[buf][c + j];
-                const float4 p2 = s2[buf][c + j], p3 = s3[buf][c + j];
+            // composite one kept particle (j: index in the batch) onto both pixels
+            auto apply = [&](const int j) {
+                const float4 p0 = s0[buf][j], p1 = s1[buf][j];
+                const float4 p2 = s2[buf][j], p3 = s3[buf][j];
                 const float2 dx = __fadd2_rn(cx, make_float2(p0.x, p0.y));
                 const float2 dy = __fadd2_rn(cy, make_float2(p0.z, p0.w));
                 const float2 d2 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
@@ -150,23 +140,27 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile,
                 w.x = d2.x < p3.z ? ex2_approx(arg.x) : 0.0f;
                 w.y = d2.y < p3.z ? ex2_approx(arg.y) : 0.0f;
                 if (MODE == SPLOTCH_ABSORPTIVE) {
-                    float2 t;
-                    if (p3.w <= kSeriesMaxA) {
-                        const float2 yn = __fmul2_rn(w, make_float2(p1.z, p1.w));
-                        const float2 q = q_series(yn);
-                        t = __ffma2_rn(yn, q, f2(1.0f));
-                        w = __fmul2_rn(w, q);
+                    const float2 na = make_float2(p1.z, p1.w);
+                    if (SERIES || p3.w <= kSeriesMaxA) {
+                        const float2 q = q_series(__fmul2_rn(w, na));
+                        w = __fmul2_rn(tacc, __fmul2_rn(w, q));
+                        tacc = __ffma2_rn(na, w, tacc);
                     } else {
                         const float2 yl = __fmul2_rn(w, f2(-1.4426950408889634f * p3.w));
-                        t = make_float2(ex2_approx(yl.x), ex2_approx(yl.y));
+                        const float2 t = make_float2(ex2_approx(yl.x), ex2_approx(yl.y));
                         w = __fmul2_rn(__fadd2_rn(f2(1.0f), make_float2(-t.x, -t.y)), f2(1.0f / p3.w));
+                        w = __fmul2_rn(tacc, w);
+                        tacc = __fmul2_rn(tacc, t);
                     }
-                    w = __fmul2_rn(tacc, w);
-                    tacc = __fmul2_rn(tacc, t);
                 }
                 cr = __ffma2_rn(w, make_float2(p2.x, p2.y), cr);
                 cg = __ffma2_rn(w, make_float2(p2.z, p2.w), cg);
                 cb = __ffma2_rn(w, make_float2(p3.x, p3.y), cb);
+            };
+            while (mask) {
+                const int j = __ffs(mask) - 1;
+                mask &= mask - 1;
+                apply(c + j);
             }
         }
         __syncthreads();
@@ -192,7 +186,8 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile,
 template <int T, int MODE, int B>
 __global__ void __launch_bounds__(T * T / 2) k_render(RenderArgs a) {
     __shared__ __align__(16) RenderSmem<B> sm;
-    render_tile<T, MODE, B>(a, blockIdx.x, sm);
+    if (MODE == SPLOTCH_ABSORPTIVE && a.hdr->series_only) render_tile<T, MODE, B, true>(a, blockIdx.x, sm);
+    else render_tile<T, MODE, B, false>(a, blockIdx.x, sm);
 }
 
 // Persistent render of the tiles of many frames: each CTA takes the next
@@ -216,9 +211,10 @@ __global__ void __launch_bounds__(T * T / 2) k_render_batch(const __grid_constan
         }
         const RenderArgs &a = args.item[lo].args;
         const int tile = (int)(task - args.item[lo].task_begin);
-        if (a.mode == SPLOTCH_EMISSION) render_tile<T, SPLOTCH_EMISSION, B>(a, tile, sm);
-        else if (a.mode == SPLOTCH_ABSORPTIVE) render_tile<T, SPLOTCH_ABSORPTIVE, B>(a, tile, sm);
-        else render_tile<T, SPLOTCH_E_EQ_A, B>(a, tile, sm);
+        if (a.mode == SPLOTCH_EMISSION) render_tile<T, SPLOTCH_EMISSION, B, false>(a, tile, sm);
+        else if (a.mode == SPLOTCH_ABSORPTIVE && a.hdr->series_only) render_tile<T, SPLOTCH_ABSORPTIVE, B, true>(a, tile, sm);
+        else if (a.mode == SPLOTCH_ABSORPTIVE) render_tile<T, SPLOTCH_ABSORPTIVE, B, false>(a, tile, sm);
+        else render_tile<T, SPLOTCH_E_EQ_A, B, false>(a, tile, sm);
     }
 }
 

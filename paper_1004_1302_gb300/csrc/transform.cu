@@ -22,6 +22,7 @@ __global__ void k_init_header(Header *hdr, Layout L, int n_species, int mode) {
     hdr->n_units = 0;
     hdr->n_species = (uint32_t)n_species;
     hdr->mode = (uint32_t)mode;
+    hdr->series_only = 0;
     for (int s = 0; s < SPLOTCH_MAX_SPECIES; ++s) {
         hdr->range_lo_enc[s] = 0xFFFFFFFFu;
         hdr->range_hi_enc[s] = 0u;
@@ -139,10 +140,14 @@ __global__ void __launch_bounds__(256) k_range(const void *v, int dtype, uint64_
 }
 
 __global__ void k_range_finish(Header *hdr, ColorizeArgs a) {
-    int s = threadIdx.x;
-    if (s >= a.n_species) return;
+    const int s = threadIdx.x;
+    const bool have = s < a.n_species;
+    const bool empty = !have || a.begin[s + 1] == a.begin[s];
+    const bool series = empty || a.sp[s].absorption <= kSeriesMaxA;
+    const bool all = __all_sync(0xFFFFFFFFu, series);
+    if (s == 0) hdr->series_only = all ? 1u : 0u;
+    if (!have) return;
     float lo = a.sp[s].lo, hi = a.sp[s].hi;
-    bool empty = a.begin[s + 1] == a.begin[s];
     if (isnan(lo)) lo = empty ? 0.0f : ordered_to_float(hdr->range_lo_enc[s]);
     if (isnan(hi)) hi = empty ? 0.0f : ordered_to_float(hdr->range_hi_enc[s]);
     hdr->lo[s] = lo;
