@@ -1,10 +1,14 @@
 // Tile renderer: one CTA per screen tile, two horizontally adjacent pixels
 // per thread.  The tile's particle list is staged in batches into shared
-// memory (prefetched into registers one batch ahead); each warp culls a
-// batch against its 8x8 pixel block with one test per lane and a ballot,
-// then walks the surviving particles in list order.  Per pixel it evaluates
-// the truncated Gaussian footprint (Section 2, first item) and integrates
-// Eq. 1 (Section 2) across the particle layer:
+// memory (prefetched into registers one batch ahead).  Each warp covers an
+// 8x8 pixel block as four groups of 8 lanes, one per 4x4 quadrant: a lane
+// tests one particle of the batch against the four quadrants, four ballots
+// give each group its own list of surviving particles, and every group walks
+// its list in list order, one particle per step, all groups in the same
+// steps (a group that is done takes a null particle that adds nothing, so the
+// steps have no branch).  Per pixel it evaluates the truncated Gaussian
+// footprint (Section 2, first item) and integrates Eq. 1 (Section 2) across
+// the particle layer:
 //   emission    C += E g
 //   absorptive  C += T_acc S, T_acc *= T, with T = exp(-A g),
 //               S = E (1 - T)/A (E g when A = 0)
@@ -44,7 +48,7 @@ __device__ __forceinline__ float2 q_series(float2 yn) {
 // with k = -log2(e)/sigma_pix^2.
 
 template <int B> struct RenderSmem {
-    float4 s0[2][B], s1[2][B], s2[2][B], s3[2][B];
+    float4 s0[2][B + 1], s1[2][B + 1], s2[2][B + 1], s3[2][B + 1];   // entry B: a particle that adds nothing
     float4 scull[2][B];   // sx, sy, r2 for the cull test
 };
 
@@ -65,12 +69,14 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile,
     const int tx = tile % a.ntx, ty = tile / a.ntx;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wx0 = tx * T + (warp % kWarpCols) * WX, wy0 = ty * T + (warp / kWarpCols) * WY;
-    const int px0 = wx0 + 2 * (lane % (WX / 2)), py = wy0 + lane / (WX / 2);
+    // lanes in four groups of 8, each on a 4x4 quadrant of the warp's block
+    const int grp = lane >> 3, gl = lane & 7;
+    const int px0 = wx0 + (grp & 1) * 4 + 2 * (gl & 1), py = wy0 + (grp >> 1) * 4 + (gl >> 1);
     const float2 cx = make_float2((float)px0 + 0.5f, (float)px0 + 1.5f);
     const float2 cy = f2((float)py + 0.5f);
-    // pixel-centre box of this warp, for the cull test
-    const float xa = (float)wx0 + 0.5f, xb = (float)(wx0 + WX) - 0.5f;
-    const float ya = (float)wy0 + 0.5f, yb = (float)(wy0 + WY) - 0.5f;
+    // pixel-centre boxes of the quadrants (left/right, top/bottom), for the cull test
+    const float xl0 = (float)wx0 + 0.5f, xl1 = (float)wx0 + 3.5f, xr0 = (float)wx0 + 4.5f, xr1 = (float)wx0 + 7.5f;
+    const float yt0 = (float)wy0 + 0.5f, yt1 = (float)wy0 + 3.5f, yb0 = (float)wy0 + 4.5f, yb1 = (float)wy0 + 7.5f;
 
     float2 cr = f2(0.f), cg = f2(0.f), cb = f2(0.f), tacc = f2(1.f);
 
@@ -108,59 +114,76 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile,
         }
     };
 
+    // null entry: r2 = 0 fails every membership test; E = 0, A = 0, k = 0 keep all terms finite
+    if (threadIdx.x < 2) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        s0[threadIdx.x][B] = z;
+        s1[threadIdx.x][B] = z;
+        s2[threadIdx.x][B] = z;
+        s3[threadIdx.x][B] = z;
+    }
     if (begin < end) {
         load(begin);
         store(0, begin);
     }
     int buf = 0;
+    // composite one kept particle (j: index in the batch) onto both pixels
+    auto apply = [&](const int j) {
+        const float4 p0 = s0[buf][j], p1 = s1[buf][j];
+        const float4 p2 = s2[buf][j], p3 = s3[buf][j];
+        const float2 dx = __fadd2_rn(cx, make_float2(p0.x, p0.y));
+        const float2 dy = __fadd2_rn(cy, make_float2(p0.z, p0.w));
+        const float2 d2 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
+        const float2 arg = __fmul2_rn(d2, make_float2(p1.x, p1.y));
+        float2 w;
+        w.x = d2.x < p3.z ? ex2_approx(arg.x) : 0.0f;
+        w.y = d2.y < p3.z ? ex2_approx(arg.y) : 0.0f;
+        if (MODE == SPLOTCH_ABSORPTIVE) {
+            const float2 na = make_float2(p1.z, p1.w);
+            if (SERIES || p3.w <= kSeriesMaxA) {
+                const float2 q = q_series(__fmul2_rn(w, na));
+                w = __fmul2_rn(tacc, __fmul2_rn(w, q));
+                tacc = __ffma2_rn(na, w, tacc);
+            } else {
+                const float2 yl = __fmul2_rn(w, f2(-1.4426950408889634f * p3.w));
+                const float2 t = make_float2(ex2_approx(yl.x), ex2_approx(yl.y));
+                w = __fmul2_rn(__fadd2_rn(f2(1.0f), make_float2(-t.x, -t.y)), f2(1.0f / p3.w));
+                w = __fmul2_rn(tacc, w);
+                tacc = __fmul2_rn(tacc, t);
+            }
+        }
+        cr = __ffma2_rn(w, make_float2(p2.x, p2.y), cr);
+        cg = __ffma2_rn(w, make_float2(p2.z, p2.w), cg);
+        cb = __ffma2_rn(w, make_float2(p3.x, p3.y), cb);
+    };
     for (uint32_t base = begin; base < end; base += B, buf ^= 1) {
         const uint32_t next = base + B;
         if (next < end) load(next);
         __syncthreads();
         const uint32_t nb = min((uint32_t)B, end - base);
         for (uint32_t c = 0; c < nb; c += 32) {
-            bool keep = false;
+            // each lane tests particle c + lane against the four quadrants
+            bool k0 = false, k1 = false, k2 = false, k3 = false;
             if (c + lane < nb) {
                 const float4 g = scull[buf][c + lane];
-                const float qx = fminf(fmaxf(g.x, xa), xb), qy = fminf(fmaxf(g.y, ya), yb);
-                const float ddx = g.x - qx, ddy = g.y - qy;
-                // conservative: a pixel that passes the exact test is never culled
-                keep = ddx * ddx + ddy * ddy <= g.z * 1.0001f + 0.01f;
+                const float lim = g.z * 1.0001f + 0.01f;   // conservative: never culls a pixel the exact test keeps
+                const float dl = g.x - fminf(fmaxf(g.x, xl0), xl1), dr = g.x - fminf(fmaxf(g.x, xr0), xr1);
+                const float dt = g.y - fminf(fmaxf(g.y, yt0), yt1), db = g.y - fminf(fmaxf(g.y, yb0), yb1);
+                const float dl2 = dl * dl, dr2 = dr * dr, dt2 = dt * dt, db2 = db * db;
+                k0 = dl2 + dt2 <= lim;
+                k1 = dr2 + dt2 <= lim;
+                k2 = dl2 + db2 <= lim;
+                k3 = dr2 + db2 <= lim;
             }
-            uint32_t mask = __ballot_sync(0xFFFFFFFFu, keep);
-            // composite one kept particle (j: index in the batch) onto both pixels
-            auto apply = [&](const int j) {
-                const float4 p0 = s0[buf][j], p1 = s1[buf][j];
-                const float4 p2 = s2[buf][j], p3 = s3[buf][j];
-                const float2 dx = __fadd2_rn(cx, make_float2(p0.x, p0.y));
-                const float2 dy = __fadd2_rn(cy, make_float2(p0.z, p0.w));
-                const float2 d2 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
-                const float2 arg = __fmul2_rn(d2, make_float2(p1.x, p1.y));
-                float2 w;
-                w.x = d2.x < p3.z ? ex2_approx(arg.x) : 0.0f;
-                w.y = d2.y < p3.z ? ex2_approx(arg.y) : 0.0f;
-                if (MODE == SPLOTCH_ABSORPTIVE) {
-                    const float2 na = make_float2(p1.z, p1.w);
-                    if (SERIES || p3.w <= kSeriesMaxA) {
-                        const float2 q = q_series(__fmul2_rn(w, na));
-                        w = __fmul2_rn(tacc, __fmul2_rn(w, q));
-                        tacc = __ffma2_rn(na, w, tacc);
-                    } else {
-                        const float2 yl = __fmul2_rn(w, f2(-1.4426950408889634f * p3.w));
-                        const float2 t = make_float2(ex2_approx(yl.x), ex2_approx(yl.y));
-                        w = __fmul2_rn(__fadd2_rn(f2(1.0f), make_float2(-t.x, -t.y)), f2(1.0f / p3.w));
-                        w = __fmul2_rn(tacc, w);
-                        tacc = __fmul2_rn(tacc, t);
-                    }
-                }
-                cr = __ffma2_rn(w, make_float2(p2.x, p2.y), cr);
-                cg = __ffma2_rn(w, make_float2(p2.z, p2.w), cg);
-                cb = __ffma2_rn(w, make_float2(p3.x, p3.y), cb);
-            };
-            while (mask) {
-                const int j = __ffs(mask) - 1;
+            const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, k0), m1 = __ballot_sync(0xFFFFFFFFu, k1);
+            const uint32_t m2 = __ballot_sync(0xFFFFFFFFu, k2), m3 = __ballot_sync(0xFFFFFFFFu, k3);
+            uint32_t mask = grp == 0 ? m0 : grp == 1 ? m1 : grp == 2 ? m2 : m3;
+            const int n_it = max(max(__popc(m0), __popc(m1)), max(__popc(m2), __popc(m3)));
+            // a group whose particles are done composites the null entry meanwhile
+            for (int it = 0; it < n_it; ++it) {
+                const int j = mask ? (int)c + __ffs(mask) - 1 : B;
                 mask &= mask - 1;
-                apply(c + j);
+                apply(j);
             }
         }
         __syncthreads();
