@@ -45,10 +45,10 @@ def parse():
     ap.add_argument("--lattice", type=int, default=1024, help="serving form: side of the resident lattice")
     ap.add_argument("--frames-only", type=int, default=0,
                     help="set up the workload, run this many frames and exit (for profilers)")
-    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batching", "serving"],
+    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batching", "serving", "split"],
                     help="plain: the headline frame; precision: 100M particles with FP16/BF16 intensity; "
                          "batching: views and snapshots in one captured graph; serving: request loop over a "
-                         "resident 1024^3 set")
+                         "resident 1024^3 set; split: split vs no split at the set sizes of Table 2")
     return ap.parse_args()
 
 
@@ -183,6 +183,88 @@ def time_frames(fr, steps, warmup, stream):
     torch.cuda.synchronize()
     t = [a.elapsed_time(b) for a, b in ev]
     return float(np.median(t)), float(np.mean(t))
+
+
+def stage_times(fr, steps, warmup, stream):
+    """Median per-stage and whole-frame times (ms) over `steps` frames."""
+    import numpy as np
+    import torch
+    for _ in range(warmup):
+        fr.run()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+    for e in ev:
+        e[0].record(stream)
+        fr.transform()
+        fr.colorize()
+        e[1].record(stream)
+        fr.sort()
+        e[2].record(stream)
+        fr.bin()
+        e[3].record(stream)
+        fr.render_tiles()
+        e[4].record(stream)
+    torch.cuda.synchronize()
+    med = lambda a, b: float(np.median([e[a].elapsed_time(e[b]) for e in ev]))
+    return {"transform_colorize": med(0, 1), "sort": med(1, 2), "bin": med(2, 3), "render": med(3, 4),
+            "frame": med(0, 4)}
+
+
+TABLE2_SIZES = (370_852, 2_646_991, 16_202_527)
+
+
+def run_split(args, dev):
+    """Split vs no-split (Section 3.2, Table 2): the three set sizes of the
+    paper's table, drawn with the 10M-particle two-species generator (60% gas,
+    40% dark matter, projected h 0.5-200 px), absorptive 1920x1080.  "Split"
+    is the default threshold ((W + H)/2 footprint pixels): the tile entries of
+    larger particles are dealt over a CTA; "no split" sets the threshold above
+    any footprint, so every particle's entries are written by one thread.
+    Tile rendering already spreads a large particle over the CTAs of its
+    tiles, so the threshold moves only the entry emission.  The two images
+    must be bit-identical.  The oracle's display rate on a bounded sample of
+    each set stands beside them."""
+    import torch
+
+    import synth
+    from oracle import oracle as O
+    from paper_1004_1302_gb300 import splotch as S
+    O.build()
+    stream = torch.cuda.current_stream(dev)
+    pal = synth.colormap()
+    rows = []
+    for n in TABLE2_SIZES:
+        n_gas = int(round(0.6 * n))
+        ps, cam = synth.config1(n_gas=n_gas, n_dm=n - n_gas)
+        dp = S.upload(ps, dev, "f32")
+        res = {"particles": n}
+        imgs = {}
+        for name, thr in (("split", 0), ("no_split", 2**31 - 1)):
+            fr = S.Frame(dp, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, large_threshold_px=thr,
+                         device=dev)
+            imgs[name] = fr.render().clone()
+            t = stage_times(fr, args.steps, max(args.warmup, 3), stream)
+            inf = fr.info()
+            res[name] = {"frame_ms": t["frame"], "bin_ms": t["bin"], "render_ms": t["render"],
+                         "large_particles": int(inf.large), "status": int(inf.status)}
+            del fr
+        res["images_identical"] = bool(torch.equal(imgs["split"], imgs["no_split"]))
+        res["split_gain"] = res["no_split"]["frame_ms"] / res["split"]["frame_ms"]
+        step = max(1, n // 400_000)
+        sub = ps.subsample(step)
+        t0 = time.perf_counter()
+        O.render_frame(sub, cam, pal, O.ABSORPTIVE, tile=16)
+        dt = time.perf_counter() - t0
+        res["cpu_oracle"] = {"particles_per_s": sub.n / dt, "display_s_for_set": n * dt / sub.n,
+                             "cores": O.num_threads(), "sample": f"every {step}th particle ({sub.n})"}
+        rows.append(res)
+        del dp, imgs
+        torch.cuda.empty_cache()
+    return {"form": "split", "metric": "display time per frame, split vs no split (1920x1080, absorptive)",
+            "unit": "ms", "higher_is_better": False,
+            "config": {"workload": "config1 generator at the set sizes of the paper's Table 2 (60% gas, 40% dark "
+                                   "matter), 1920x1080, absorptive", "tile": args.tile, "batch": args.batch},
+            "sets": rows}
 
 
 def run_precision(args, dev):
@@ -411,7 +493,8 @@ def main():
         dist.barrier()
     S.load()
     if args.form != "plain":
-        runner = {"precision": run_precision, "batching": run_batching, "serving": run_serving}[args.form]
+        runner = {"precision": run_precision, "batching": run_batching, "serving": run_serving,
+                  "split": run_split}[args.form]
         res = runner(args, dev)
         if rank == 0:
             print(json.dumps(res), flush=True)

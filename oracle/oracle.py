@@ -67,6 +67,10 @@ def _load():
         lib.oracle_colour.argtypes = [ctypes.c_size_t, P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_int, P, ctypes.c_int, P, P, P]
         lib.oracle_colour.restype = None
+        lib.oracle_colour_vector.argtypes = [ctypes.c_size_t, P, P, P, P, P, ctypes.c_double, ctypes.c_double, P, P]
+        lib.oracle_colour_vector.restype = None
+        lib.oracle_modulate.argtypes = [ctypes.c_size_t, P, ctypes.c_double, P, P]
+        lib.oracle_modulate.restype = None
         lib.oracle_order.argtypes = [ctypes.c_size_t, P, P, ctypes.c_int, P]
         lib.oracle_order.restype = ctypes.c_size_t
         lib.oracle_tile_lists.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, P, P, P, P]
@@ -140,8 +144,10 @@ def value_range(v, use_log: bool) -> tuple[float, float]:
     return lo.value, hi.value
 
 
-def colour(v, species, palette) -> tuple[np.ndarray, np.ndarray, list]:
-    """Per-particle E and A (n x 3, float64) and the (lo, hi) used per species."""
+def colour(v, species, palette, vec=None, q=None) -> tuple[np.ndarray, np.ndarray, list]:
+    """Per-particle E and A (n x 3, float64) and the (lo, hi) used per species.
+    A species with `use_vector` takes E from the components of `vec` (n x 3),
+    one with `modulate` scales E and A by q over the species' largest q."""
     lib = _load()
     vd = np.ascontiguousarray(v, dtype=np.float64)
     n = vd.size
@@ -162,12 +168,25 @@ def colour(v, species, palette) -> tuple[np.ndarray, np.ndarray, list]:
         ranges.append((lo, hi))
         if seg.size == 0:
             continue
-        fixed = np.ascontiguousarray(s.fixed_rgb, dtype=np.float64)
         e = np.empty((seg.size, 3), np.float64)
         a = np.empty((seg.size, 3), np.float64)
-        seg = np.ascontiguousarray(seg)
-        lib.oracle_colour(seg.size, _p(seg), int(s.use_log), float(lo), float(hi), float(s.brightness),
-                          float(s.absorption), int(s.use_colormap), _p(fixed), pal.shape[0], _p(pal), _p(e), _p(a))
+        if getattr(s, "use_vector", 0):
+            comp = [np.ascontiguousarray(vec[s.begin:s.end, c], dtype=np.float64) for c in range(3)]
+            vr = [value_range(cc, False) for cc in comp]
+            vlo = np.array([r[0] for r in vr], np.float64)
+            vhi = np.array([r[1] for r in vr], np.float64)
+            lib.oracle_colour_vector(seg.size, *[_p(cc) for cc in comp], _p(vlo), _p(vhi), float(s.brightness),
+                                     float(s.absorption), _p(e), _p(a))
+        else:
+            fixed = np.ascontiguousarray(s.fixed_rgb, dtype=np.float64)
+            seg = np.ascontiguousarray(seg)
+            lib.oracle_colour(seg.size, _p(seg), int(s.use_log), float(lo), float(hi), float(s.brightness),
+                              float(s.absorption), int(s.use_colormap), _p(fixed), pal.shape[0], _p(pal), _p(e),
+                              _p(a))
+        if getattr(s, "modulate", 0):
+            qs = np.ascontiguousarray(q[s.begin:s.end], dtype=np.float64)
+            _, q_max = value_range(qs, False)
+            lib.oracle_modulate(seg.size, _p(qs), float(q_max), _p(e), _p(a))
         E[s.begin:s.end] = e
         A[s.begin:s.end] = a
     return E, A, ranges
@@ -214,7 +233,7 @@ def render_frame(ps, cam, palette, mode: int, tile: int = 16, sigma_per_h: float
     (H x W x 3 float64), or the composite of selected pixels ((i, j) pairs)."""
     lib = _load()
     geo = geometry(cam, ps.x, ps.y, ps.z, ps.h, sigma_per_h, trunc_f)
-    E, A, ranges = colour(ps.v, ps.species, palette)
+    E, A, ranges = colour(ps.v, ps.species, palette, getattr(ps, "vec", None), getattr(ps, "q", None))
     ordr = order(geo, by_depth=(mode == ABSORPTIVE))
     offsets, lst = tile_lists(cam.width, cam.height, tile, ordr, geo.bbox)
     img = None

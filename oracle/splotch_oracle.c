@@ -11,7 +11,9 @@
  *     cut to zero beyond f * sigma_p (Section 2, first item);
  *   - red, green and blue are transported independently (Section 2, second item);
  *   - the intensity along a ray obeys dI/dx = (E_p - A_p I) rho_p(x) (Section 2, Eq. 1);
- *   - E_p comes from a scalar through a colour look-up table (Section 2, third item);
+ *   - E_p comes from a scalar through a colour look-up table, or from the three
+ *     components of a vector quantity, and a particle's optical depth may be
+ *     scaled by another scalar (Section 2, third item);
  *   - the "process" stage normalises particle values and the "display" stage
  *     transforms to screen coordinates, colours and renders (Section 3.2).
  *
@@ -196,6 +198,43 @@ void oracle_colour(size_t n, const double *v, int use_log, double lo, double hi,
         for (int c = 0; c < 3; ++c) {
             E[3 * i + c] = brightness * rgb[c];
             A[3 * i + c] = absorption;
+        }
+    }
+}
+
+/* Vector colouring (Section 2, third item: a vector quantity's three
+ * components give the red, green and blue of E).  Reading: each component is
+ * normalised like a scalar without the logarithm (C7 per component, over the
+ * particles of the species): t_c = clamp((v_c - lo_c)/(hi_c - lo_c), 0, 1),
+ * t_c = 0 if hi_c == lo_c; E_c = brightness * t_c, A = absorption * (1, 1, 1).
+ * vx, vy, vz hold the components as doubles. */
+void oracle_colour_vector(size_t n, const double *vx, const double *vy, const double *vz, const double lo[3],
+                          const double hi[3], double brightness, double absorption, double *E, double *A)
+{
+    const double *v[3] = {vx, vy, vz};
+    for (size_t i = 0; i < n; ++i) {
+        for (int c = 0; c < 3; ++c) {
+            double t = hi[c] > lo[c] ? (v[c][i] - lo[c]) / (hi[c] - lo[c]) : 0.0;
+            t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+            E[3 * i + c] = brightness * t;
+            A[3 * i + c] = absorption;
+        }
+    }
+}
+
+/* Optical-depth modulation (Section 2, third item: the optical depth of a
+ * particle made proportional to another scalar q).  Reading: q scales the
+ * particle's column density rho_0 (C5 sets rho_0 = 1) to m = clamp(q / q_max,
+ * 0, 1), q_max the largest q of the species (m = 0 if q_max <= 0).  In Eq. 1
+ * rho multiplies both terms, so E and A are both scaled by m. */
+void oracle_modulate(size_t n, const double *q, double q_max, double *E, double *A)
+{
+    for (size_t i = 0; i < n; ++i) {
+        double m = q_max > 0.0 ? q[i] / q_max : 0.0;
+        m = m < 0.0 ? 0.0 : (m > 1.0 ? 1.0 : m);
+        for (int c = 0; c < 3; ++c) {
+            E[3 * i + c] *= m;
+            A[3 * i + c] *= m;
         }
     }
 }

@@ -113,17 +113,22 @@ class Species:
     fixed_rgb: tuple = (1.0, 1.0, 1.0)
     lo: float = float("nan")
     hi: float = float("nan")
+    use_vector: int = 0     # E from the three components of the particle vector
+    modulate: int = 0       # optical depth scaled by the particle scalar q
 
 
 @dataclass
 class ParticleSet:
-    """Structure-of-arrays particle block (x, y, z, h, intensity), float32."""
+    """Structure-of-arrays particle block (x, y, z, h, intensity), float32;
+    optionally a vector quantity (n x 3) and a second scalar q."""
     x: np.ndarray
     y: np.ndarray
     z: np.ndarray
     h: np.ndarray
     v: np.ndarray
     species: list = field(default_factory=list)
+    vec: np.ndarray | None = None
+    q: np.ndarray | None = None
 
     @property
     def n(self) -> int:
@@ -140,7 +145,8 @@ class ParticleSet:
             pos += idx.size
             species.append(sp)
         idx = np.concatenate(parts) if parts else np.zeros(0, dtype=np.int64)
-        return ParticleSet(self.x[idx], self.y[idx], self.z[idx], self.h[idx], self.v[idx], species)
+        return ParticleSet(self.x[idx], self.y[idx], self.z[idx], self.h[idx], self.v[idx], species,
+                           None if self.vec is None else self.vec[idx], None if self.q is None else self.q[idx])
 
 
 @dataclass
@@ -279,3 +285,14 @@ def colormap(k: int = 256) -> np.ndarray:
     (t, t^2, t^4) with t = j / (k - 1).  Shape (k, 3), float32."""
     t = np.arange(k, dtype=np.float64) / (k - 1)
     return np.stack([t, t * t, t ** 4], axis=1).astype(np.float32)
+
+
+def vector_fields(ps: ParticleSet, seed: int = SEED) -> ParticleSet:
+    """The same particles with a vector quantity (velocity-like components,
+    uniform in [-1, 1] from the counter-based generator) and a density-like
+    second scalar q = (h_min / h)^3 attached."""
+    n = ps.n
+    vec = np.stack([uniform(seed, 0x300 + c, 0, n, -1.0, 1.0) for c in range(3)], axis=1).astype(np.float32)
+    h = ps.h.astype(np.float64)
+    q = ((h.min() / h) ** 3).astype(np.float32) if n else np.zeros(0, np.float32)
+    return ParticleSet(ps.x, ps.y, ps.z, ps.h, ps.v, ps.species, vec, q)

@@ -329,6 +329,76 @@ def test_colour_ends_and_linear_ramp(oracle_mod):
     np.testing.assert_allclose(E3[:, 0], np.clip((v - 1.0) / 2.0, 0, 1), atol=1e-13)
 
 
+# --- vector colouring and optical-depth modulation (Section 2, third item) ---
+
+def _vec_species(n, **kw):
+    return [Species(0, n, use_log=0, brightness=kw.pop("brightness", 1.5), absorption=kw.pop("absorption", 0.0),
+                    use_colormap=0, use_vector=kw.pop("use_vector", 1), modulate=kw.pop("modulate", 0))]
+
+
+def test_vector_colour_ends_channels_and_affine_invariance(oracle_mod):
+    O = oracle_mod
+    rng = np.random.default_rng(11)
+    n = 500
+    vec = rng.normal(size=(n, 3))
+    v = np.ones(n)
+    pal = synth.colormap()
+    E, A, _ = O.colour(v, _vec_species(n, absorption=0.2), pal, vec, None)
+    for c in range(3):
+        # the ends of each component map to 0 and to the brightness, in that channel only
+        assert E[vec[:, c].argmin(), c] == 0.0 and E[vec[:, c].argmax(), c] == pytest.approx(1.5, rel=1e-15)
+    assert (E >= 0).all() and (E <= 1.5 + 1e-15).all()
+    np.testing.assert_array_equal(A, 0.2)
+    # each channel depends on its own component only
+    vec2 = vec.copy()
+    vec2[:, 1] = rng.permutation(vec2[:, 1])
+    E2, _, _ = O.colour(v, _vec_species(n), pal, vec2, None)
+    np.testing.assert_array_equal(E2[:, [0, 2]], E[:, [0, 2]])
+    assert not np.allclose(E2[:, 1], E[:, 1])
+    # normalisation removes any positive scale and offset of a component
+    vec3 = vec * np.array([3.0, 0.25, 7.0]) + np.array([-5.0, 2.0, 0.5])
+    E3, _, _ = O.colour(v, _vec_species(n), pal, vec3, None)
+    np.testing.assert_allclose(E3, E, rtol=1e-12, atol=1e-14)
+    # three particles on the component axes: red, green and blue in turn
+    axes = np.eye(3)
+    Ea, _, _ = O.colour(np.ones(3), _vec_species(3, brightness=1.0), pal, axes, None)
+    np.testing.assert_array_equal(Ea, np.eye(3))
+
+
+def test_modulation_is_proportional_and_keeps_the_source_function(oracle_mod):
+    O = oracle_mod
+    cam = _axis_cam(97, 49)
+    s = O.camera(cam).scale
+    h = 4.0 * 2.0 / s                     # sigma_pix = 4 at depth 2
+    xs = [0.5 - 0.25, 0.5 + 0.25]         # two particles far apart on screen
+    def frame(q, mode, E, A):
+        sp = [Species(0, 2, use_log=0, brightness=E, absorption=A, use_colormap=0, fixed_rgb=(1.0, 0.5, 0.25),
+                      modulate=1)]
+        ps = ParticleSet(*[np.asarray(a, np.float32) for a in (xs, [0.5, 0.5], [0.5, 0.5], [h, h], [1.0, 1.0])],
+                         sp, None, np.asarray(q, np.float32))
+        return O.render_frame(ps, cam, synth.colormap(), mode).image
+    base = frame([1.0, 1.0], 0, 0.8, 0.0)
+    mod = frame([1.0, 0.25], 0, 0.8, 0.0)
+    # q_max = 1: the first particle is unchanged, the second scaled by q / q_max = 1/4
+    left, right = base[:, :48], base[:, 49:]
+    np.testing.assert_allclose(mod[:, :48], left, rtol=1e-15)
+    np.testing.assert_allclose(mod[:, 49:], 0.25 * right, rtol=1e-14)
+    # only the ratio to the species' largest q matters
+    np.testing.assert_allclose(frame([8.0, 2.0], 0, 0.8, 0.0), mod, rtol=1e-14)
+    # an optically thick layer shows E / A whatever the modulation; a thin one scales with it
+    geo = O.geometry(cam, np.float32(xs), np.float32([0.5, 0.5]), np.float32([0.5, 0.5]), np.float32([h, h]))
+    (i0, i1), j = np.floor(geo.sx).astype(int), int(np.floor(geo.sy[0]))
+    thick = frame([1.0, 0.5], 1, 0.7, 80.0)
+    centre = np.array([1.0, 0.5, 0.25]) * 0.7 / 80.0
+    np.testing.assert_allclose(thick[j, i0], centre, rtol=1e-9)
+    np.testing.assert_allclose(thick[j, i1], centre, rtol=1e-9)
+    thin = frame([1.0, 0.5], 1, 0.7, 1e-9)
+    np.testing.assert_allclose(thin[:, 49:], 0.5 * frame([1.0, 1.0], 1, 0.7, 1e-9)[:, 49:], rtol=1e-8)
+    # q <= 0 removes a particle
+    assert frame([1.0, 0.0], 2, 0.7, 0.7)[:, 49:].max() == 0.0
+    assert np.abs(frame([1.0, -2.0], 1, 0.7, 0.3)[:, 49:]).max() == 0.0
+
+
 # --- tiles, culling and brute force -----------------------------------------
 
 def _numpy_brute(geo, E, A, ordr, W, H, mode):
