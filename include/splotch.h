@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define SPLOTCH_ABI_VERSION 1
+#define SPLOTCH_ABI_VERSION 2
 #define SPLOTCH_MAX_SPECIES 8
 #define SPLOTCH_MAX_PALETTE 256
 
@@ -60,15 +60,21 @@ typedef enum { SPLOTCH_EMISSION = 0, SPLOTCH_ABSORPTIVE = 1, SPLOTCH_E_EQ_A = 2 
 
 /* Particle block in structure-of-arrays form, one array per property, as in
  * the block file layout of Section 3.1.  Species are contiguous index ranges
- * [species_begin[s], species_begin[s+1]). */
+ * [species_begin[s], species_begin[s+1]).  The vector quantity and the
+ * modulating scalar (Section 2, third item) are optional: NULL when no
+ * species uses them. */
 typedef struct {
     uint64_t n;                 /* number of particles, < 2^32 */
     const float *x, *y, *z;     /* device, n each: world position */
     const float *h;             /* device, n: smoothing length */
     const void *intensity;      /* device, n values of intensity_dtype: the scalar mapped to colour */
-    int32_t intensity_dtype;    /* splotch_dtype */
+    int32_t intensity_dtype;    /* splotch_dtype, also the type of vector[] and modulator */
     int32_t n_species;          /* 1..SPLOTCH_MAX_SPECIES */
     uint64_t species_begin[SPLOTCH_MAX_SPECIES + 1];  /* host values; begin[0] = 0, begin[n_species] = n */
+    const void *vector[3];      /* device, n values each, or NULL: components of a vector quantity
+                                   (for example velocity) for species with use_vector */
+    const void *modulator;      /* device, n values, or NULL: scalar q (for example density) for
+                                   species with modulate */
 } splotch_particles;
 
 /* Perspective camera.  The caller fills eye, target, up, fov_x_deg (full
@@ -98,6 +104,12 @@ typedef struct {
     float brightness;        /* E = brightness * colour */
     float absorption;        /* A = absorption * (1, 1, 1); 0 = pure emission */
     float fixed_rgb[3];
+    int32_t use_vector;      /* 1: E_c = brightness * t_c, t_c = clamp((v_c - lo_c)/(hi_c - lo_c), 0, 1),
+                                lo_c/hi_c = min/max of component c over the species (a vector quantity
+                                mapped to red, green and blue, Section 2, third item); overrides use_colormap */
+    int32_t modulate;        /* 1: the particle's column density, and so E and A, scaled by
+                                m = clamp(q / q_max, 0, 1), q_max = max of q over the species
+                                (m = 0 if q_max <= 0): optical depth proportional to q (Section 2, third item) */
 } splotch_species;
 
 typedef struct {
@@ -173,7 +185,12 @@ int splotch_transform(const splotch_particles *p, const splotch_camera *cam, con
  * species when lo or hi is NaN; t = clamp((u - lo)/(hi - lo), 0, 1) (0 when
  * hi == lo); palette value by linear interpolation, w = t (K - 1),
  * k = min(floor(w), K - 2); E = brightness * colour (or * fixed_rgb),
- * A = absorption.  Half-precision intensity is widened to float exactly.
+ * A = absorption.  A species with use_vector takes E from the three
+ * components of p->vector instead, each normalised linearly over the
+ * species; one with modulate scales E and A by q / q_max of the species
+ * (p->modulator).  Half-precision values are widened to float exactly.
+ * Errors: SPLOTCH_ERR_ARG when a species asks for a vector or modulator
+ * array that p does not provide.
  */
 int splotch_colorize(const splotch_particles *p, const splotch_species *species, const splotch_colormap *cmap,
                      void *workspace, size_t workspace_bytes, void *stream);

@@ -61,6 +61,9 @@ struct Header {
     uint32_t range_lo_enc[SPLOTCH_MAX_SPECIES];   // order-preserving encodings for atomic min/max
     uint32_t range_hi_enc[SPLOTCH_MAX_SPECIES];
     float lo[SPLOTCH_MAX_SPECIES], hi[SPLOTCH_MAX_SPECIES];
+    uint32_t vlo_enc[SPLOTCH_MAX_SPECIES][3], vhi_enc[SPLOTCH_MAX_SPECIES][3];   // vector components
+    uint32_t qlo_enc[SPLOTCH_MAX_SPECIES], qhi_enc[SPLOTCH_MAX_SPECIES];         // modulating scalar
+    float vlo[SPLOTCH_MAX_SPECIES][3], vhi[SPLOTCH_MAX_SPECIES][3], qmax[SPLOTCH_MAX_SPECIES];
     Layout layout;
 };
 
@@ -83,6 +86,8 @@ struct TransformArgs {
 
 struct ColorizeArgs {
     const void *v;
+    const void *vec[3];        // vector components (species with use_vector)
+    const void *q;             // modulating scalar (species with modulate)
     int dtype;
     uint64_t n;
     int n_species;

@@ -233,9 +233,16 @@ int splotch_colorize(const splotch_particles *p, const splotch_species *species,
     if (p->species_begin[0] != 0 || p->species_begin[p->n_species] != p->n) return SPLOTCH_ERR_ARG;
     for (int s = 0; s < p->n_species; ++s)
         if (p->species_begin[s + 1] < p->species_begin[s]) return SPLOTCH_ERR_ARG;
+    for (int s = 0; s < p->n_species; ++s) {
+        if (p->species_begin[s + 1] == p->species_begin[s]) continue;
+        if (species[s].use_vector && (!p->vector[0] || !p->vector[1] || !p->vector[2])) return SPLOTCH_ERR_ARG;
+        if (species[s].modulate && !p->modulator) return SPLOTCH_ERR_ARG;
+    }
     if (workspace_bytes < col_offset(p->n) + p->n * 16) return SPLOTCH_ERR_WORKSPACE;
     ColorizeArgs a{};
     a.v = p->intensity;
+    for (int c = 0; c < 3; ++c) a.vec[c] = p->vector[c];
+    a.q = p->modulator;
     a.dtype = p->intensity_dtype;
     a.n = p->n;
     a.n_species = p->n_species;

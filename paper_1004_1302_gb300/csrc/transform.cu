@@ -28,6 +28,15 @@ __global__ void k_init_header(Header *hdr, Layout L, int n_species, int mode) {
         hdr->range_hi_enc[s] = 0u;
         hdr->lo[s] = 0.0f;
         hdr->hi[s] = 0.0f;
+        for (int c = 0; c < 3; ++c) {
+            hdr->vlo_enc[s][c] = 0xFFFFFFFFu;
+            hdr->vhi_enc[s][c] = 0u;
+            hdr->vlo[s][c] = 0.0f;
+            hdr->vhi[s][c] = 0.0f;
+        }
+        hdr->qlo_enc[s] = 0xFFFFFFFFu;
+        hdr->qhi_enc[s] = 0u;
+        hdr->qmax[s] = 0.0f;
     }
     hdr->layout = L;
 }
@@ -119,10 +128,10 @@ __global__ void __launch_bounds__(256) k_transform(TransformArgs a, float4 *geo,
     }
 }
 
-// Range pre-pass of one species: min/max of u (log10 of the value, or the
-// value) into the header's order-preserving slots.
+// Range pre-pass of one quantity of one species: min/max of u (log10 of the
+// value, or the value) into two of the header's order-preserving slots.
 __global__ void __launch_bounds__(256) k_range(const void *v, int dtype, uint64_t begin, uint64_t end, int use_log,
-                                               Header *hdr, int s) {
+                                               uint32_t *lo_enc, uint32_t *hi_enc) {
     float lo = INFINITY, hi = -INFINITY;
     for (uint64_t i = begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < end;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -134,8 +143,8 @@ __global__ void __launch_bounds__(256) k_range(const void *v, int dtype, uint64_
     uint32_t elo = __reduce_min_sync(0xFFFFFFFFu, float_to_ordered(lo));
     uint32_t ehi = __reduce_max_sync(0xFFFFFFFFu, float_to_ordered(hi));
     if (lane_id() == 0) {
-        atomicMin(&hdr->range_lo_enc[s], elo);
-        atomicMax(&hdr->range_hi_enc[s], ehi);
+        atomicMin(lo_enc, elo);
+        atomicMax(hi_enc, ehi);
     }
 }
 
@@ -152,6 +161,12 @@ __global__ void k_range_finish(Header *hdr, ColorizeArgs a) {
     if (isnan(hi)) hi = empty ? 0.0f : ordered_to_float(hdr->range_hi_enc[s]);
     hdr->lo[s] = lo;
     hdr->hi[s] = hi;
+    if (a.sp[s].use_vector && !empty)
+        for (int c = 0; c < 3; ++c) {
+            hdr->vlo[s][c] = ordered_to_float(hdr->vlo_enc[s][c]);
+            hdr->vhi[s][c] = ordered_to_float(hdr->vhi_enc[s][c]);
+        }
+    if (a.sp[s].modulate && !empty) hdr->qmax[s] = ordered_to_float(hdr->qhi_enc[s]);
 }
 
 __global__ void __launch_bounds__(256) k_colorize(ColorizeArgs a, const Header *hdr, float4 *col) {
@@ -165,7 +180,18 @@ __global__ void __launch_bounds__(256) k_colorize(ColorizeArgs a, const Header *
         while (s + 1 < a.n_species && i >= a.begin[s + 1]) ++s;
         const splotch_species &sp = a.sp[s];
         float r, g, b;
-        if (sp.use_colormap) {
+        if (sp.use_vector) {
+            // each component normalised linearly over the species
+            float t[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float u = load_value(a.vec[c], a.dtype, i);
+                const float lo = hdr->vlo[s][c], hi = hdr->vhi[s][c];
+                const float tc = hi > lo ? __fdiv_rn(u - lo, hi - lo) : 0.0f;
+                t[c] = fminf(fmaxf(tc, 0.0f), 1.0f);
+            }
+            r = t[0]; g = t[1]; b = t[2];
+        } else if (sp.use_colormap) {
             float u = load_value(a.v, a.dtype, i);
             if (sp.use_log) u = log10f(fmaxf(u, 1e-37f));
             const float lo = hdr->lo[s], hi = hdr->hi[s];
@@ -180,7 +206,15 @@ __global__ void __launch_bounds__(256) k_colorize(ColorizeArgs a, const Header *
         } else {
             r = sp.fixed_rgb[0]; g = sp.fixed_rgb[1]; b = sp.fixed_rgb[2];
         }
-        col[i] = make_float4(sp.brightness * r, sp.brightness * g, sp.brightness * b, sp.absorption);
+        float m = 1.0f;
+        if (sp.modulate) {
+            // column density scaled by q / q_max of the species: E and A alike
+            const float qm = hdr->qmax[s];
+            m = qm > 0.0f ? __fdiv_rn(load_value(a.q, a.dtype, i), qm) : 0.0f;
+            m = fminf(fmaxf(m, 0.0f), 1.0f);
+        }
+        col[i] = make_float4(m * (sp.brightness * r), m * (sp.brightness * g), m * (sp.brightness * b),
+                             m * sp.absorption);
     }
 }
 
@@ -232,8 +266,26 @@ cudaError_t launch_colorize(const ColorizeArgs &a, void *ws, const Layout &L, cu
         if (e <= b || !(isnan(sp.lo) || isnan(sp.hi))) continue;
         uint64_t blocks = (e - b + 255) / 256;
         int grid = (int)(blocks < (uint64_t)sms * 4 ? blocks : (uint64_t)sms * 4);
-        k_range<<<grid, 256, 0, st>>>(a.v, a.dtype, b, e, sp.use_log, header(ws), s);
+        k_range<<<grid, 256, 0, st>>>(a.v, a.dtype, b, e, sp.use_log, &header(ws)->range_lo_enc[s],
+                                       &header(ws)->range_hi_enc[s]);
         count_launches(1);
+    }
+    for (int s = 0; s < a.n_species; ++s) {
+        const splotch_species &sp = a.sp[s];
+        const uint64_t b = a.begin[s], e = a.begin[s + 1];
+        if (e <= b) continue;
+        uint64_t blocks = (e - b + 255) / 256;
+        int grid = (int)(blocks < (uint64_t)sms * 4 ? blocks : (uint64_t)sms * 4);
+        if (sp.use_vector)
+            for (int c = 0; c < 3; ++c) {
+                k_range<<<grid, 256, 0, st>>>(a.vec[c], a.dtype, b, e, 0, &header(ws)->vlo_enc[s][c],
+                                               &header(ws)->vhi_enc[s][c]);
+                count_launches(1);
+            }
+        if (sp.modulate) {
+            k_range<<<grid, 256, 0, st>>>(a.q, a.dtype, b, e, 0, &header(ws)->qlo_enc[s], &header(ws)->qhi_enc[s]);
+            count_launches(1);
+        }
     }
     k_range_finish<<<1, 32, 0, st>>>(header(ws), a);
     count_launches(1);

@@ -75,7 +75,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 class Particles(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
                 ("h", ctypes.c_void_p), ("intensity", ctypes.c_void_p), ("intensity_dtype", ctypes.c_int32),
-                ("n_species", ctypes.c_int32), ("species_begin", ctypes.c_uint64 * (MAX_SPECIES + 1))]
+                ("n_species", ctypes.c_int32), ("species_begin", ctypes.c_uint64 * (MAX_SPECIES + 1)),
+                ("vector", ctypes.c_void_p * 3), ("modulator", ctypes.c_void_p)]
 
 
 class Camera(ctypes.Structure):
@@ -93,7 +94,7 @@ class Colormap(ctypes.Structure):
 class SpeciesParams(ctypes.Structure):
     _fields_ = [("use_log", ctypes.c_int32), ("use_colormap", ctypes.c_int32), ("lo", ctypes.c_float),
                 ("hi", ctypes.c_float), ("brightness", ctypes.c_float), ("absorption", ctypes.c_float),
-                ("fixed_rgb", ctypes.c_float * 3)]
+                ("fixed_rgb", ctypes.c_float * 3), ("use_vector", ctypes.c_int32), ("modulate", ctypes.c_int32)]
 
 
 class RenderParams(ctypes.Structure):
@@ -321,6 +322,8 @@ def make_species(sp) -> SpeciesParams:
     s.brightness = float(sp.brightness)
     s.absorption = float(sp.absorption)
     s.fixed_rgb[:] = [float(v) for v in sp.fixed_rgb]
+    s.use_vector = int(getattr(sp, "use_vector", 0))
+    s.modulate = int(getattr(sp, "modulate", 0))
     return s
 
 
@@ -347,6 +350,8 @@ class DeviceParticles:
     v: object
     dtype: str
     species: list = field(default_factory=list)
+    vec: list | None = None      # three tensors (components of a vector quantity), intensity dtype
+    q: object = None             # modulating scalar, intensity dtype
 
     @property
     def n(self) -> int:
@@ -362,17 +367,30 @@ class DeviceParticles:
         for k, s in enumerate(self.species):
             p.species_begin[k] = int(s.begin)
         p.species_begin[len(self.species)] = self.n
+        if self.vec is not None and self.n:
+            for c in range(3):
+                p.vector[c] = self.vec[c].data_ptr()
+        if self.q is not None and self.n:
+            p.modulator = self.q.data_ptr()
         return p
 
 
 def upload(ps, device="cuda", dtype: str = "f32", stream=None) -> DeviceParticles:
     """Copy a host ParticleSet (numpy float32 arrays) to the device; the
-    intensity is stored as f32, f16 or bf16 (round to nearest even)."""
+    intensity (and the optional vector and modulator) is stored as f32, f16
+    or bf16 (round to nearest even)."""
+    import numpy as np
     import torch
     tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[dtype]
     cols = [torch.from_numpy(a).to(device, non_blocking=False) for a in (ps.x, ps.y, ps.z, ps.h)]
     v = torch.from_numpy(ps.v).to(device).to(tdt)
-    return DeviceParticles(*cols, v, dtype, list(ps.species))
+    vec = q = None
+    if getattr(ps, "vec", None) is not None:
+        vec = [torch.from_numpy(np.ascontiguousarray(ps.vec[:, c], dtype=np.float32)).to(device).to(tdt)
+               for c in range(3)]
+    if getattr(ps, "q", None) is not None:
+        q = torch.from_numpy(np.ascontiguousarray(ps.q, dtype=np.float32)).to(device).to(tdt)
+    return DeviceParticles(*cols, v, dtype, list(ps.species), vec, q)
 
 
 def rounded_intensity(ps, dtype: str):

@@ -58,11 +58,24 @@ def gpu_render(ps, cam, palette, mode, dtype="f32", tile=16, batch=128, large_th
                      img, info)
 
 
+def _as_stored(a, dtype):
+    """Values as the device stores them in `dtype` (float64 numpy)."""
+    import torch
+    if a is None:
+        return None
+    if dtype == "f32":
+        return np.asarray(a, np.float64)
+    tdt = {"f16": torch.float16, "bf16": torch.bfloat16}[dtype]
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(tdt).to(torch.float64).numpy()
+
+
 def oracle_render(ps, cam, palette, mode, dtype="f32", tile=16, trunc_f=2.0, pixels=None, image=True):
-    """The oracle on the intensities exactly as the device stores them."""
+    """The oracle on the intensities (and the vector and modulating scalar,
+    if any) exactly as the device stores them."""
     from paper_1004_1302_gb300 import splotch as S
     v = S.rounded_intensity(ps, dtype)
-    ps2 = synth.ParticleSet(ps.x, ps.y, ps.z, ps.h, v, ps.species)
+    ps2 = synth.ParticleSet(ps.x, ps.y, ps.z, ps.h, v, ps.species, _as_stored(getattr(ps, "vec", None), dtype),
+                            _as_stored(getattr(ps, "q", None), dtype))
     return O.render_frame(ps2, cam, palette, mode, tile=tile, trunc_f=trunc_f, pixels=pixels, image=image)
 
 

@@ -30,7 +30,7 @@ def test_exports_every_declared_function(S):
     for name in declared:
         assert hasattr(lib, name), name
     assert set(declared) == set(S.EXPORTS)
-    assert lib.splotch_abi_version() == 1
+    assert lib.splotch_abi_version() == 2
 
 
 def test_status_strings(S):
