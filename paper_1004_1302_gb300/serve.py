@@ -61,6 +61,9 @@ class RenderServer:
                  memory_budget: int | None = None, max_inflight: int = 8, keep_images: bool = False, device="cuda",
                  h_typical: float | None = None, trunc_f: float = 2.0):
         import torch
+        if getattr(species, "use_vector", 0) or getattr(species, "modulate", 0):
+            raise ValueError("the region cut carries positions, h and the scalar intensity only: "
+                             "vector colouring and optical-depth modulation are not served")
         self.torch = torch
         self.device = torch.device(device)
         self.resident = resident
