@@ -45,10 +45,11 @@ def parse():
     ap.add_argument("--lattice", type=int, default=1024, help="serving form: side of the resident lattice")
     ap.add_argument("--frames-only", type=int, default=0,
                     help="set up the workload, run this many frames and exit (for profilers)")
-    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batching", "serving", "split"],
+    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batching", "serving", "split", "io"],
                     help="plain: the headline frame; precision: 100M particles with FP16/BF16 intensity; "
                          "batching: views and snapshots in one captured graph; serving: request loop over a "
-                         "resident 1024^3 set; split: split vs no split at the set sizes of Table 2")
+                         "resident 1024^3 set; split: split vs no split at the set sizes of Table 2; io: snapshots read "
+                         "from block files, loading overlapped with rendering")
     return ap.parse_args()
 
 
@@ -265,6 +266,105 @@ def run_split(args, dev):
             "config": {"workload": "config1 generator at the set sizes of the paper's Table 2 (60% gas, 40% dark "
                                    "matter), 1920x1080, absorptive", "tile": args.tile, "batch": args.batch},
             "sets": rows}
+
+
+def run_io(args, dev):
+    """Read stage (Section 3, stage a; Section 3.1 block files): snapshots of
+    the 10M-particle workload written as block files (x, y, z, h, intensity;
+    5 x 10M floats, 200 MB each) and loaded through the pinned double-buffered
+    loader.  Reported: the loader's read-and-copy rate alone, frames/s when
+    every snapshot is loaded and then rendered, and frames/s when snapshot
+    k + 1 loads on a copy stream while snapshot k renders.  The files are
+    read right after being written, so they come from the page cache."""
+    import tempfile
+
+    import torch
+
+    import synth
+    from paper_1004_1302_gb300 import splotch as S
+    K = 4
+    tmp = tempfile.mkdtemp(prefix="splotch_io_")
+    pal = synth.colormap()
+    snaps, paths = [], []
+    for k in range(K):
+        ps, cam = synth.config1(seed=synth.SEED + k)
+        snaps.append(ps)
+        paths.append(os.path.join(tmp, f"snap{k}.bin"))
+        synth.write_block_file(paths[-1], [ps.x, ps.y, ps.z, ps.h, ps.v])
+    n = snaps[0].n
+    species = list(snaps[0].species)
+    bufs = [[torch.empty(n, dtype=torch.float32, device=dev) for _ in range(5)] for _ in range(2)]
+    copy, comp = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    loader = S.Loader(chunk_bytes=32 << 20)
+    files = [S.block_file(p, 5, n) for p in paths]
+    frames = [None, None]
+    with torch.cuda.stream(comp):
+        for b in range(2):
+            frames[b] = S.Frame(S.DeviceParticles(*bufs[b], "f32", species), cam, pal, S.ABSORPTIVE,
+                                tile=args.tile, batch=args.batch, device=dev)
+    # size the tile-entry capacity of both frames once
+    for b in range(2):
+        loader.start(files[b], range(5), bufs[b], 0, n, copy.cuda_stream)
+        loader.wait()
+        copy.synchronize()
+        frames[b].render(comp)
+    torch.cuda.synchronize()
+
+    def load_only():
+        t0 = time.perf_counter()
+        for k in range(K):
+            loader.start(files[k], range(5), bufs[k % 2], 0, n, copy.cuda_stream)
+            loader.wait()
+            copy.synchronize()
+        return time.perf_counter() - t0
+
+    def sequential():
+        t0 = time.perf_counter()
+        for k in range(K):
+            loader.start(files[k], range(5), bufs[k % 2], 0, n, copy.cuda_stream)
+            loader.wait()
+            comp.wait_stream(copy)
+            frames[k % 2].run(comp)
+            comp.synchronize()
+        return time.perf_counter() - t0
+
+    def overlapped():
+        t0 = time.perf_counter()
+        loader.start(files[0], range(5), bufs[0], 0, n, copy.cuda_stream)
+        loader.wait()
+        for k in range(K):
+            comp.wait_stream(copy)
+            if k + 1 < K:
+                copy.wait_stream(comp)
+                loader.start(files[k + 1], range(5), bufs[(k + 1) % 2], 0, n, copy.cuda_stream)
+            frames[k % 2].run(comp)
+            if k + 1 < K:
+                loader.wait()
+        comp.synchronize()
+        copy.synchronize()
+        return time.perf_counter() - t0
+
+    reps = max(1, args.steps // 4)
+    load_only()
+    t_load = min(load_only() for _ in range(reps))
+    sequential()
+    t_seq = min(sequential() for _ in range(reps))
+    overlapped()
+    t_ovl = min(overlapped() for _ in range(reps))
+    status = [int(fr.info().status) for fr in frames]
+    loader.close()
+    for p in paths:
+        os.remove(p)
+    os.rmdir(tmp)
+    file_bytes = 5 * 4 * n
+    return {"form": "io", "metric": "frames/s with the read stage (1920x1080, absorptive)", "unit": "frames/s",
+            "higher_is_better": True,
+            "config": {"workload": f"{K} snapshots of config1 (10M particles) as block files, 5 blocks x 10M "
+                                   "float32 (200 MB each), page-cache reads", "tile": args.tile,
+                       "batch": args.batch, "chunk_bytes": 32 << 20},
+            "load_GBps": K * file_bytes / t_load / 1e9, "load_ms_per_snapshot": 1e3 * t_load / K,
+            "sequential_frames_per_s": K / t_seq, "overlapped_frames_per_s": K / t_ovl,
+            "overlap_gain": t_seq / t_ovl, "status": status, "host_cores": os.cpu_count()}
 
 
 def run_precision(args, dev):
@@ -494,7 +594,7 @@ def main():
     S.load()
     if args.form != "plain":
         runner = {"precision": run_precision, "batching": run_batching, "serving": run_serving,
-                  "split": run_split}[args.form]
+                  "split": run_split, "io": run_io}[args.form]
         res = runner(args, dev)
         if rank == 0:
             print(json.dumps(res), flush=True)

@@ -47,7 +47,8 @@ typedef enum {
     SPLOTCH_ERR_WORKSPACE = -3,   /* workspace too small (on the host) or tile entries over capacity (device) */
     SPLOTCH_ERR_TIMEOUT = -4,     /* a bounded device wait ran out */
     SPLOTCH_ERR_OOM_ADMISSION = -5,
-    SPLOTCH_ERR_STATE = -6        /* workspace does not hold the step this call needs */
+    SPLOTCH_ERR_STATE = -6,       /* workspace does not hold the step this call needs */
+    SPLOTCH_ERR_IO = -7           /* a file could not be opened or read (short file, I/O error) */
 } splotch_status;
 
 typedef enum { SPLOTCH_F32 = 0, SPLOTCH_F16 = 1, SPLOTCH_BF16 = 2 } splotch_dtype;
@@ -332,6 +333,63 @@ uint64_t splotch_launch_count(void);
  */
 #define SPLOTCH_NO_ALLOC_MAX_KEYS (1u << 18)
 int splotch_sort_keys_no_alloc(const uint32_t *key, uint32_t n, uint32_t *order, uint32_t *count, void *stream);
+
+/*
+ * Block-structured particle files (Section 3.1, MPI implementation): a file
+ * holds n_blocks contiguous blocks, one per particle property, each of
+ * n_particles 32-bit floats; seen as a 2-D array A of n_blocks x n_particles
+ * floats (row-major), block b, particle i is at byte
+ * offset + 4 (b n_particles + i).  A reader takes the same slice
+ * [first, first + count) of each block it needs (the n x N/nprocs subarray
+ * of a process), converting the byte order when the file's differs from the
+ * host's.  Host-side I/O: these calls are the "read" stage of Section 3,
+ * outside the rendering path.
+ */
+typedef struct {
+    const char *path;          /* host, NUL-terminated */
+    uint64_t offset;           /* byte offset of block 0 in the file */
+    int32_t n_blocks;          /* n: properties per particle */
+    int32_t big_endian;        /* 1: the file stores big-endian floats; 0: little-endian */
+    uint64_t n_particles;      /* N: floats per block */
+} splotch_block_file;
+
+/* Read particles [first, first + count) of block `block` into host memory
+ * (count floats, caller-owned, any alignment), in host byte order.
+ * Synchronous.  Errors: SPLOTCH_ERR_ARG (block or range outside the file
+ * description, NULL pointers), SPLOTCH_ERR_IO (open/read failure, file
+ * shorter than the description). */
+int splotch_block_read(const splotch_block_file *file, int32_t block, uint64_t first, uint64_t count, float *dst);
+
+/* Loader: reads block slices on host threads of its own, each into two
+ * pinned staging buffers (chunk_bytes each, allocated at creation), and
+ * enqueues their copies to device arrays on the caller's stream, so a file's
+ * read overlaps the copies and whatever else runs on the device (for example
+ * the render of the previous snapshot on another stream).  Reader t takes
+ * chunks t, t + T, ... of a load.  One load at a time per loader. */
+typedef struct splotch_loader splotch_loader;
+
+/* Create a loader on the current CUDA device with n_threads readers (1..64).
+ * chunk_bytes: multiple of 4, at least 4096.  Errors: SPLOTCH_ERR_ARG,
+ * SPLOTCH_ERR_CUDA (pinned allocation failed). */
+int splotch_loader_create(size_t chunk_bytes, int32_t n_threads, splotch_loader **out);
+
+/* Start loading: for d < n_dst, particles [first, first + count) of block
+ * blocks[d] go to device array dst[d] (count floats each, device memory
+ * owned by the caller, host byte order).  Returns at once; the copies are
+ * ordered on `stream` (a cudaStream_t as void*).  The arrays and `file`'s
+ * path must stay valid until splotch_loader_wait returns.  Errors:
+ * SPLOTCH_ERR_ARG (bad description or range, a load already running). */
+int splotch_loader_start(splotch_loader *loader, const splotch_block_file *file, int32_t n_dst,
+                         const int32_t *blocks, uint64_t first, uint64_t count, float *const *dst, void *stream);
+
+/* Wait for the host side of the current load (every chunk read and its copy
+ * enqueued) and return its status (SPLOTCH_ERR_IO on a read failure; the
+ * arrays are then incomplete).  The device copies complete in stream order.
+ * Without a running load, returns the status of the last one. */
+int splotch_loader_wait(splotch_loader *loader);
+
+/* Free the staging buffers (waits for a running load first). */
+int splotch_loader_destroy(splotch_loader *loader);
 
 #ifdef __cplusplus
 }

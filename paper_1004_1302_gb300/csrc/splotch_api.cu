@@ -150,6 +150,7 @@ const char *splotch_status_string(int status) {
     case SPLOTCH_ERR_TIMEOUT: return "bounded device wait ran out";
     case SPLOTCH_ERR_OOM_ADMISSION: return "request refused: not enough memory";
     case SPLOTCH_ERR_STATE: return "workspace does not hold the required step";
+    case SPLOTCH_ERR_IO: return "file could not be opened or read";
     default: return "unknown status";
     }
 }

@@ -19,10 +19,10 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "_splotch.so")
-SOURCES = ["splotch_api.cu", "transform.cu", "sort.cu", "bin.cu", "render.cu", "roi.cu", "no_alloc.cu"]
+SOURCES = ["splotch_api.cu", "transform.cu", "sort.cu", "bin.cu", "render.cu", "roi.cu", "no_alloc.cu", "io.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-OK, ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_TIMEOUT, ERR_OOM_ADMISSION, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+OK, ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_TIMEOUT, ERR_OOM_ADMISSION, ERR_STATE, ERR_IO = 0, -1, -2, -3, -4, -5, -6, -7
 F32, F16, BF16 = 0, 1, 2
 EMISSION, ABSORPTIVE, E_EQ_A = 0, 1, 2
 MAX_SPECIES = 8
@@ -112,6 +112,11 @@ class BatchItem(ctypes.Structure):
 MAX_BATCH = 128
 
 
+class BlockFile(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_char_p), ("offset", ctypes.c_uint64), ("n_blocks", ctypes.c_int32),
+                ("big_endian", ctypes.c_int32), ("n_particles", ctypes.c_uint64)]
+
+
 class FrameInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("visible", ctypes.c_uint32), ("tile_entries", ctypes.c_uint64),
                 ("large", ctypes.c_uint32), ("ntiles", ctypes.c_uint32), ("lo", ctypes.c_float * MAX_SPECIES),
@@ -123,7 +128,8 @@ EXPORTS = ["splotch_abi_version", "splotch_status_string", "splotch_camera_init"
            "splotch_render_tiles", "splotch_frame_info", "splotch_get_keys", "splotch_get_geometry",
            "splotch_get_order", "splotch_get_tile_lists", "splotch_get_colors", "splotch_count_fragments",
            "splotch_launch_count", "splotch_sort_keys_no_alloc", "splotch_render_tiles_batch",
-           "splotch_roi_scratch_size", "splotch_roi_count", "splotch_roi_select"]
+           "splotch_roi_scratch_size", "splotch_roi_count", "splotch_roi_select", "splotch_block_read",
+           "splotch_loader_create", "splotch_loader_start", "splotch_loader_wait", "splotch_loader_destroy"]
 
 _lib = None
 
@@ -162,6 +168,11 @@ def load(path: str | None = None):
         "splotch_roi_scratch_size": ([U64, P(ctypes.c_size_t)], I32),
         "splotch_roi_count": ([P(Particles), P(ctypes.c_double), V, ctypes.c_size_t, V, V], I32),
         "splotch_roi_select": ([P(Particles), P(ctypes.c_double), V, ctypes.c_size_t, V, V, V, V, V, U64, V, V], I32),
+        "splotch_block_read": ([P(BlockFile), ctypes.c_int32, U64, U64, V], I32),
+        "splotch_loader_create": ([ctypes.c_size_t, ctypes.c_int32, P(V)], I32),
+        "splotch_loader_start": ([V, P(BlockFile), ctypes.c_int32, P(ctypes.c_int32), U64, U64, P(V), V], I32),
+        "splotch_loader_wait": ([V], I32),
+        "splotch_loader_destroy": ([V], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -284,6 +295,62 @@ def splotch_roi_select(src: Particles, box, scratch: int, scratch_bytes: int, x,
                        count: int, stream: int):
     _check(load().splotch_roi_select(ctypes.byref(src), _box(box), scratch, scratch_bytes, x, y, z, h, v, capacity,
                                      count, stream), "splotch_roi_select")
+
+
+# --- block-structured particle files (Section 3.1) ------------------------------
+
+def block_file(path: str, n_blocks: int, n_particles: int, big_endian: bool = False, offset: int = 0) -> BlockFile:
+    f = BlockFile()
+    f._path = os.fsencode(path)          # keeps the bytes alive as long as the struct
+    f.path = f._path
+    f.offset, f.n_blocks, f.big_endian, f.n_particles = int(offset), int(n_blocks), int(big_endian), int(n_particles)
+    return f
+
+
+def splotch_block_read(f: BlockFile, block: int, first: int, count: int):
+    """Particles [first, first + count) of one block, host byte order (numpy float32)."""
+    import numpy as np
+    out = np.empty(count, np.float32)
+    _check(load().splotch_block_read(ctypes.byref(f), block, first, count, out.ctypes.data if count else None),
+           "splotch_block_read")
+    return out
+
+
+class Loader:
+    """Pinned double-buffered loader of block slices into device arrays
+    (`threads` host threads inside the library read while copies run on the
+    stream)."""
+
+    def __init__(self, chunk_bytes: int = 16 << 20, threads: int = 4):
+        h = ctypes.c_void_p()
+        _check(load().splotch_loader_create(chunk_bytes, threads, ctypes.byref(h)), "splotch_loader_create")
+        self._h = h
+        self._keep = None
+
+    def start(self, f: BlockFile, blocks, dst, first: int, count: int, stream: int = 0):
+        """Load block blocks[d] into the float32 device tensor dst[d]."""
+        n = len(blocks)
+        b = (ctypes.c_int32 * max(n, 1))(*blocks)
+        d = (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in dst])
+        self._keep = (f, b, d, list(dst))
+        _check(load().splotch_loader_start(self._h, ctypes.byref(f), n, b, first, count, d, stream),
+               "splotch_loader_start")
+
+    def wait(self):
+        st = load().splotch_loader_wait(self._h)
+        self._keep = None
+        _check(st, "splotch_loader_wait")
+
+    def close(self):
+        if self._h:
+            _check(load().splotch_loader_destroy(self._h), "splotch_loader_destroy")
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 NO_ALLOC_MAX_KEYS = 1 << 18

@@ -296,3 +296,14 @@ def vector_fields(ps: ParticleSet, seed: int = SEED) -> ParticleSet:
     h = ps.h.astype(np.float64)
     q = ((h.min() / h) ** 3).astype(np.float32) if n else np.zeros(0, np.float32)
     return ParticleSet(ps.x, ps.y, ps.z, ps.h, ps.v, ps.species, vec, q)
+
+
+def write_block_file(path: str, arrays, big_endian: bool = False, offset_bytes: int = 0) -> None:
+    """Write float arrays (one per property, equal length) as a block file:
+    `offset_bytes` zero bytes, then each property's N floats contiguously,
+    in the given byte order."""
+    dt = np.dtype(">f4" if big_endian else "<f4")
+    with open(path, "wb") as f:
+        f.write(b"\0" * offset_bytes)
+        for a in arrays:
+            np.ascontiguousarray(a, dtype=np.float32).astype(dt).tofile(f)
