@@ -560,14 +560,11 @@ def cpu_baseline(ps, cam, pal):
     import synth  # noqa: F401
     from oracle import oracle as O
     O.build()
-    step = 8
-    sub = ps.subsample(step)
     t0 = time.perf_counter()
-    O.render_frame(sub, cam, pal, O.ABSORPTIVE, tile=16)
+    O.render_frame(ps, cam, pal, O.ABSORPTIVE, tile=16)
     dt = time.perf_counter() - t0
-    return {"value": sub.n / dt, "unit": "particles/s", "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"every {step}th particle of each species ({sub.n} of {ps.n}), one full 1920x1080 "
-                      f"absorptive frame, {dt:.1f} s"}
+    return {"value": ps.n / dt, "unit": "particles/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"the whole workload ({ps.n} particles), one full 1920x1080 absorptive frame, {dt:.1f} s"}
 
 
 def main():
