@@ -591,3 +591,69 @@ class Frame:
         out = t.empty((max(self.dp.n, 1), 4), dtype=t.float32, device=self.device)
         splotch_get_colors(self.ws.data_ptr(), self.ws_bytes, out.data_ptr(), self.stream_ptr())
         return out[:self.dp.n]
+
+
+class HostPipeline:
+    """Frames whose particles come from host memory: the host-to-device copy
+    of a frame's inputs runs on a copy stream while the previous frame renders
+    on the compute stream (two sets of device arrays), and each image is read
+    back to its own pinned host buffer on a third stream.  `submit` enqueues one frame and
+    returns its host image (valid after `synchronize`).  The host arrays
+    should be pinned for the copies to overlap."""
+
+    def __init__(self, n: int, species, cam_spec, palette, mode: int, dtype: str = "f32", tile: int = 16,
+                 batch: int = 128, max_tile_entries: int | None = None, device="cuda"):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[dtype]
+        self.sets = [[torch.empty(n, dtype=torch.float32, device=self.device) for _ in range(4)] +
+                     [torch.empty(n, dtype=tdt, device=self.device)] for _ in range(2)]
+        self.frames = [Frame(DeviceParticles(*cols, dtype, list(species)), cam_spec, palette, mode, tile=tile,
+                             batch=batch, max_tile_entries=max_tile_entries, device=self.device)
+                       for cols in self.sets]
+        self.images = [torch.empty((int(cam_spec.height), int(cam_spec.width), 3), dtype=torch.float32).pin_memory()
+                       for _ in range(2)]
+        self.copy = torch.cuda.Stream(self.device)
+        self.readback = torch.cuda.Stream(self.device)
+        self.compute = torch.cuda.current_stream(self.device)
+        self.copied = [torch.cuda.Event() for _ in range(2)]
+        self.done = [torch.cuda.Event() for _ in range(2)]
+        self.read = [torch.cuda.Event() for _ in range(2)]
+        self.k = 0
+
+    def submit(self, host_cols):
+        """Enqueue one frame from host arrays (x, y, z, h, intensity tensors)."""
+        b = self.k % 2
+        self.k += 1
+        self.copy.wait_event(self.done[b])            # frame k - 2 has finished with these arrays
+        with self.torch.cuda.stream(self.copy):
+            for d, h in zip(self.sets[b], host_cols):
+                d.copy_(h, non_blocking=True)
+        self.copied[b].record(self.copy)
+        self.compute.wait_event(self.copied[b])
+        self.compute.wait_event(self.read[b])         # frame k - 2's image has been read back
+        fr = self.frames[b]
+        fr.run(self.compute)
+        self.done[b].record(self.compute)
+        self.readback.wait_event(self.done[b])
+        with self.torch.cuda.stream(self.readback):
+            self.images[b].copy_(fr.image, non_blocking=True)
+        self.read[b].record(self.readback)
+        return self.images[b]
+
+    def size(self, host_cols, max_retries: int = 3):
+        """Size both frames' tile-entry capacity on these inputs (synchronising)."""
+        for b in range(2):
+            for d, h in zip(self.sets[b], host_cols):
+                d.copy_(h)
+            self.frames[b].render(self.compute, max_retries)
+        self.synchronize()
+
+    def info(self, b: int = 0) -> FrameInfo:
+        return self.frames[b].info(self.compute)
+
+    def synchronize(self):
+        self.copy.synchronize()
+        self.compute.synchronize()
+        self.readback.synchronize()

@@ -102,3 +102,28 @@ def test_pipeline_images_equal_direct_uploads(tmp_path):
     torch.cuda.synchronize()
     for g, d in zip(got, direct):
         np.testing.assert_array_equal(g.cpu().numpy(), d)
+
+
+def test_host_pipeline_images_equal_direct_renders():
+    """Frames from pinned host arrays, the copy of frame k + 1 overlapping the
+    render of frame k: each image equals a direct render of its particles."""
+    import torch
+    from paper_1004_1302_gb300 import splotch as S
+    S.load()
+    snaps = [synth.config1(n_gas=90_000, n_dm=60_000, width=300, height=180, seed=synth.SEED + k) for k in range(4)]
+    pal = synth.colormap()
+    cam = snaps[0][1]
+    direct = [S.Frame(S.upload(ps, "cuda", "f32"), cam, pal, S.ABSORPTIVE).render().cpu().numpy() for ps, _ in snaps]
+    hosts = [[torch.from_numpy(a).pin_memory() for a in (ps.x, ps.y, ps.z, ps.h, ps.v)] for ps, _ in snaps]
+    pipe = S.HostPipeline(snaps[0][0].n, snaps[0][0].species, cam, pal, S.ABSORPTIVE)
+    pipe.size(hosts[0])
+    got = []
+    for k in range(4):
+        img = pipe.submit(hosts[k])
+        if k % 2 == 1:                     # both host images of the pair are final after a synchronize
+            pipe.synchronize()
+            got += [pipe.images[0].numpy().copy(), pipe.images[1].numpy().copy()]
+    assert pipe.info(0).status == 0 and pipe.info(1).status == 0
+    for g, d in zip(got, direct):
+        np.testing.assert_array_equal(g, d)
+    assert img.shape == (180, 300, 3)
