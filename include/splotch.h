@@ -133,6 +133,8 @@ typedef struct {
     uint32_t large;               /* particles sent to the cooperative emission path */
     uint32_t ntiles;
     float lo[SPLOTCH_MAX_SPECIES], hi[SPLOTCH_MAX_SPECIES];   /* normalisation range used */
+    uint32_t check_line;          /* library built with device index checks: source line of the first
+                                     failed check (status then SPLOTCH_ERR_STATE); 0 otherwise */
 } splotch_frame_info_t;
 
 /* Library ABI version (SPLOTCH_ABI_VERSION). */

@@ -44,7 +44,10 @@ __global__ void __launch_bounds__(256) k_bin_reduce(BinArgs a) {
     uint64_t beg, end;
     bin_range(a.ctas, n, &beg, &end);
     unsigned long long sum = 0;
-    for (uint64_t k = beg + threadIdx.x; k < end; k += blockDim.x) sum += cells_of(a.box[list[k]], a.sshift);
+    for (uint64_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
+        const uint32_t p = list[k];
+        if (SPL_CHECK(a.hdr, p < a.hdr->layout.n)) sum += cells_of(a.box[p], a.sshift);
+    }
     unsigned long long tot;
     block_exclusive_scan64<256>(sum, ws, &tot);
     if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
@@ -117,9 +120,11 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
             tb[q] = make_ushort4(1, 1, 0, 0);
             if (j < m) {
                 p[q] = list[step + j];
-                const ushort4 b = a.box[p[q]];
-                tb[q] = make_ushort4(b.x >> a.sshift, b.y >> a.sshift, b.z >> a.sshift, b.w >> a.sshift);
-                nt = (uint32_t)(tb[q].z - tb[q].x + 1) * (uint32_t)(tb[q].w - tb[q].y + 1);
+                if (SPL_CHECK(a.hdr, p[q] < a.hdr->layout.n)) {
+                    const ushort4 b = a.box[p[q]];
+                    tb[q] = make_ushort4(b.x >> a.sshift, b.y >> a.sshift, b.z >> a.sshift, b.w >> a.sshift);
+                    nt = (uint32_t)(tb[q].z - tb[q].x + 1) * (uint32_t)(tb[q].w - tb[q].y + 1);
+                }
             }
             const bool big = nt > a.large_tiles;
             const uint32_t inc = warp_inclusive_scan(nt);
@@ -282,7 +287,9 @@ __global__ void __launch_bounds__(256) k_fine_count(FineArgs a) {
     if (threadIdx.x < (kSuperSide + 1) * (kSuperSide + 1)) (&diff[0][0])[threadIdx.x] = 0;
     __syncthreads();
     for (uint32_t i = un.y + threadIdx.x; i < un.z; i += 256) {
-        const FineRect f = fine_rect(a.box[a.sval[i]], a.tshift, ox, oy);
+        const uint32_t p = a.sval[i];
+        if (!SPL_CHECK(a.hdr, p < a.hdr->layout.n)) continue;
+        const FineRect f = fine_rect(a.box[p], a.tshift, ox, oy);
         atomicAdd(&diff[f.r0][f.c0], 1);
         atomicAdd(&diff[f.r0][f.c1 + 1], -1);
         atomicAdd(&diff[f.r1 + 1][f.c0], -1);
@@ -416,7 +423,7 @@ __global__ void __launch_bounds__(256) k_fine_emit(FineArgs a) {
         FineRect f{1, 0, 1, 0};                      // empty
         if (i < un.z) {
             p = a.sval[i];
-            f = fine_rect(a.box[p], a.tshift, ox, oy);
+            if (SPL_CHECK(a.hdr, p < a.hdr->layout.n)) f = fine_rect(a.box[p], a.tshift, ox, oy);
         }
         const uint32_t rows = f.r0 <= f.r1 ? (0xFFu >> (kSuperSide - 1 - f.r1)) & (0xFFu << f.r0) : 0u;
         const uint32_t cols = f.c0 <= f.c1 ? (0xFFu >> (kSuperSide - 1 - f.c1)) & (0xFFu << f.c0) : 0u;

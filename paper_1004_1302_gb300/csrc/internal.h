@@ -58,6 +58,7 @@ struct Header {
     uint32_t n_species;
     uint32_t mode;
     uint32_t series_only;      // every species with particles has A <= kSeriesMaxA
+    uint32_t check_line;       // checked builds: source line of the first failed index check (0: none)
     uint32_t range_lo_enc[SPLOTCH_MAX_SPECIES];   // order-preserving encodings for atomic min/max
     uint32_t range_hi_enc[SPLOTCH_MAX_SPECIES];
     float lo[SPLOTCH_MAX_SPECIES], hi[SPLOTCH_MAX_SPECIES];
@@ -68,6 +69,26 @@ struct Header {
 };
 
 constexpr uint64_t kHeaderBytes = 4096;
+
+// Index checks of the checked build (-DSPLOTCH_DEVICE_CHECKS): a failed check
+// records its source line and SPLOTCH_ERR_STATE in the header and the caller
+// skips the access (no trap).  In the release build the condition is not
+// evaluated and the check is always true.
+#ifdef __CUDACC__
+__device__ __forceinline__ bool device_check(const Header *hdr, bool ok, int line) {
+    if (!ok) {
+        Header *h = const_cast<Header *>(hdr);
+        atomicCAS(&h->check_line, 0u, (uint32_t)line);
+        atomicExch(&h->status, (int)SPLOTCH_ERR_STATE);
+    }
+    return ok;
+}
+#ifdef SPLOTCH_DEVICE_CHECKS
+#define SPL_CHECK(hdr, cond) (::spl::device_check((hdr), (cond), __LINE__))
+#else
+#define SPL_CHECK(hdr, cond) (true)
+#endif
+#endif
 
 // Absorption up to which the renderer takes a layer's source and transmission
 // from a series in A g instead of an exponential.

@@ -46,6 +46,7 @@ __global__ void k_na_init(Header *hdr) {
     hdr->key_min = kInvalidKey;
     hdr->key_max = 0;
     hdr->sorted_buf = 0;
+    hdr->check_line = 0;
 }
 
 __global__ void __launch_bounds__(256) k_na_stats(const uint32_t *key, uint32_t n, Header *hdr) {

@@ -91,10 +91,12 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile,
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const uint32_t j = threadIdx.x + q * kThreads;
-            if (j < nb) {
+            if (j < nb && SPL_CHECK(a.hdr, base + j < a.hdr->layout.cap)) {
                 const uint32_t p = __ldg(&a.list[base + j]);
-                rg[q] = __ldg(&a.geo[p]);
-                rc[q] = __ldg(&a.col[p]);
+                if (SPL_CHECK(a.hdr, p < a.hdr->layout.n)) {
+                    rg[q] = __ldg(&a.geo[p]);
+                    rc[q] = __ldg(&a.col[p]);
+                }
             }
         }
     };

@@ -201,8 +201,10 @@ __global__ void __launch_bounds__(kDsThreads) k_radix_downsweep(RadixPass P) {
             const uint32_t k = skey[j];
             const uint32_t d = ((k - kmin) >> P.shift) & P.mask;
             const uint32_t pos = base[d] + (j - lstart[d]);
-            P.key_out[pos] = k;
-            P.val_out[pos] = sval[j];
+            if (SPL_CHECK(P.hdr, pos < n)) {
+                P.key_out[pos] = k;
+                P.val_out[pos] = sval[j];
+            }
         }
         __syncthreads();
         if (owns_digit) base[threadIdx.x] += ltot[threadIdx.x];

@@ -373,6 +373,7 @@ int splotch_frame_info(const void *workspace, size_t workspace_bytes, splotch_fr
     info->tile_entries = h.tile_entries;
     info->large = h.n_large;
     info->ntiles = h.layout.ntiles;
+    info->check_line = h.check_line;
     for (int k = 0; k < SPLOTCH_MAX_SPECIES; ++k) {
         info->lo[k] = h.lo[k];
         info->hi[k] = h.hi[k];

@@ -23,6 +23,7 @@ __global__ void k_init_header(Header *hdr, Layout L, int n_species, int mode) {
     hdr->n_species = (uint32_t)n_species;
     hdr->mode = (uint32_t)mode;
     hdr->series_only = 0;
+    hdr->check_line = 0;
     for (int s = 0; s < SPLOTCH_MAX_SPECIES; ++s) {
         hdr->range_lo_enc[s] = 0xFFFFFFFFu;
         hdr->range_hi_enc[s] = 0u;

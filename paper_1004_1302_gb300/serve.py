@@ -17,11 +17,15 @@ calls and owns the device buffers (through PyTorch).
 from __future__ import annotations
 
 import math
+import threading
 import time
 from collections import deque
 from dataclasses import dataclass, field
 
 from . import splotch as S
+
+# Server-level statuses (not library codes): a request cancelled by its client.
+CANCELLED = -100
 
 
 @dataclass
@@ -39,6 +43,7 @@ class Request:
     retries: int = 0
     cap_hint: int = 0           # tile-entry capacity the device asked for after an overflow
     image: object = None        # kept only when the server keeps images
+    cancel_after: float | None = None   # the client cancels this many seconds after arrival
 
     @property
     def latency(self) -> float:
@@ -54,17 +59,22 @@ class _Slot:
     frame: object = None
     cut: list = field(default_factory=list)
     event: object = None
+    quarantined: bool = False   # its request timed out; the slot waits for the device work to end
+    cancelled: bool = False     # its request was cancelled while running; the result is dropped
 
 
 class RenderServer:
     def __init__(self, resident, palette, species, tile: int = 16, batch: int = 128, large_threshold_px: int = 0,
                  memory_budget: int | None = None, max_inflight: int = 8, keep_images: bool = False, device="cuda",
-                 h_typical: float | None = None, trunc_f: float = 2.0):
+                 h_typical: float | None = None, trunc_f: float = 2.0, request_timeout_s: float | None = None):
         import torch
         if getattr(species, "use_vector", 0) or getattr(species, "modulate", 0):
             raise ValueError("the region cut carries positions, h and the scalar intensity only: "
                              "vector colouring and optical-depth modulation are not served")
         self.torch = torch
+        self.request_timeout_s = request_timeout_s
+        self._cancel = set()
+        self._cancel_lock = threading.Lock()
         self.device = torch.device(device)
         self.resident = resident
         self.src = resident.struct()
@@ -154,8 +164,21 @@ class RenderServer:
         slot.req, slot.frame, slot.cut, slot.event = req, fr, cut + [v], ev
         return True
 
+    def _release(self, slot: _Slot):
+        self.in_use -= slot.req.bytes
+        slot.req = slot.frame = slot.event = None
+        slot.cut = []
+        slot.quarantined = slot.cancelled = False
+
     def _finish(self, slot: _Slot, now: float, queue: deque) -> Request | None:
         req, fr = slot.req, slot.frame
+        if slot.quarantined:            # reported at its timeout; now its buffers can go
+            self._release(slot)
+            return None
+        if slot.cancelled:
+            req.status, req.done = CANCELLED, now
+            self._release(slot)
+            return req
         info = fr.info(slot.stream)
         self.in_use -= req.bytes
         done = None
@@ -174,24 +197,61 @@ class RenderServer:
         slot.cut = []
         return done
 
+    # --- cancellation -----------------------------------------------------
+    def cancel(self, rid: int):
+        """Cancel request `rid` (from any thread): a waiting request leaves the
+        queue, a running one has its result dropped when its work ends."""
+        with self._cancel_lock:
+            self._cancel.add(rid)
+
+    def _cancelled(self, req: Request, now: float) -> bool:
+        if req.cancel_after is not None and now >= req.arrival + req.cancel_after:
+            return True
+        with self._cancel_lock:
+            return req.rid in self._cancel
+
     # --- the loop ------------------------------------------------------------
     def serve(self, requests, clock=time.perf_counter, idle_sleep: float = 1e-4):
         """Serve `requests` (each with its arrival time, seconds after the
-        start).  Returns (finished requests, statistics)."""
+        start).  Returns (finished requests, statistics).  A running request
+        whose work has not ended `request_timeout_s` after admission is
+        reported with ERR_TIMEOUT (watchdog on its completion event); its slot
+        and memory stay reserved until the device work ends."""
+        for slot in self.slots:         # slots left quarantined by an earlier call
+            if slot.req is not None and slot.quarantined and slot.event.query():
+                self._release(slot)
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         queue: deque = deque()
         finished = []
         t0 = clock()
-        while pending or queue or any(s.req is not None for s in self.slots):
+        # (slots quarantined after a timeout do not hold the loop: a later call releases them)
+        while pending or queue or any(s.req is not None and not s.quarantined for s in self.slots):
             now = clock() - t0
             while pending and pending[0].arrival <= now:
                 queue.append(pending.popleft())
             progressed = False
+            for req in [r for r in queue if self._cancelled(r, now)]:
+                queue.remove(req)
+                req.status, req.done = CANCELLED, now
+                finished.append(req)
+                progressed = True
             for slot in self.slots:
-                if slot.req is not None and slot.event.query():
+                if slot.req is None:
+                    continue
+                if slot.event.query():
                     r = self._finish(slot, clock() - t0, queue)
                     if r is not None:
                         finished.append(r)
+                    progressed = True
+                    continue
+                if not slot.quarantined and not slot.cancelled and self._cancelled(slot.req, now):
+                    slot.cancelled = True
+                if (self.request_timeout_s is not None and not slot.quarantined
+                        and now - slot.req.admitted > self.request_timeout_s):
+                    req = slot.req
+                    req.status, req.done = S.ERR_TIMEOUT, now
+                    finished.append(req)
+                    slot.quarantined = True
                     progressed = True
             while queue:
                 free = [s for s in self.slots if s.req is None]
@@ -233,6 +293,8 @@ class RenderServer:
         pct = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)] if lat else None
         return {"requests": len(finished), "completed": len(ok),
                 "refused": sum(r.status == S.ERR_OOM_ADMISSION for r in finished),
+                "timed_out": sum(r.status == S.ERR_TIMEOUT for r in finished),
+                "cancelled": sum(r.status == CANCELLED for r in finished),
                 "wall_s": wall, "frames_per_s": len(ok) / wall if wall > 0 else None,
                 "particles_per_s": sum(r.n for r in ok) / wall if wall > 0 else None,
                 "p50_ms": pct(0.50) * 1e3 if lat else None, "p99_ms": pct(0.99) * 1e3 if lat else None,

@@ -19,6 +19,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "_splotch.so")
+LIB_PATH_CHECKED = os.path.join(_HERE, "_splotch_checked.so")
 SOURCES = ["splotch_api.cu", "transform.cu", "sort.cu", "bin.cu", "render.cu", "roi.cu", "no_alloc.cu", "io.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -35,20 +36,23 @@ def _nvcc() -> str:
     return "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
     """Compile the CUDA sources for sm_103a (one object per file, in
-    parallel) and link ``_splotch.so`` next to this file."""
+    parallel) and link ``_splotch.so`` next to this file.  checked=True
+    builds ``_splotch_checked.so`` instead: the same library with device
+    index checks (-DSPLOTCH_DEVICE_CHECKS), for tests."""
+    lib_path = LIB_PATH_CHECKED if checked else LIB_PATH
     srcs = [os.path.join(_CSRC, s) for s in SOURCES]
     deps = srcs + [os.path.join(_CSRC, "internal.h"), os.path.join(_CSRC, "device_util.cuh"),
                    os.path.join(_INCLUDE, "splotch.h")]
-    if not force and os.path.exists(LIB_PATH):
-        t = os.path.getmtime(LIB_PATH)
+    if not force and os.path.exists(lib_path):
+        t = os.path.getmtime(lib_path)
         if all(os.path.getmtime(d) <= t for d in deps):
-            return LIB_PATH
-    objdir = os.path.join(_HERE, "_build")
+            return lib_path
+    objdir = os.path.join(_HERE, "_build_checked" if checked else "_build")
     os.makedirs(objdir, exist_ok=True)
     common = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
-              "-I", _INCLUDE, "-I", _CSRC]
+              "-I", _INCLUDE, "-I", _CSRC] + (["-DSPLOTCH_DEVICE_CHECKS"] if checked else [])
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
@@ -62,12 +66,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB_PATH + ".tmp"
+    tmp = lib_path + ".tmp"
     r = subprocess.run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 # --- structs (mirror include/splotch.h) -------------------------------------
@@ -120,7 +124,7 @@ class BlockFile(ctypes.Structure):
 class FrameInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("visible", ctypes.c_uint32), ("tile_entries", ctypes.c_uint64),
                 ("large", ctypes.c_uint32), ("ntiles", ctypes.c_uint32), ("lo", ctypes.c_float * MAX_SPECIES),
-                ("hi", ctypes.c_float * MAX_SPECIES)]
+                ("hi", ctypes.c_float * MAX_SPECIES), ("check_line", ctypes.c_uint32)]
 
 
 EXPORTS = ["splotch_abi_version", "splotch_status_string", "splotch_camera_init", "splotch_workspace_size",
@@ -139,7 +143,7 @@ def load(path: str | None = None):
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or LIB_PATH
+    p = path or (LIB_PATH_CHECKED if os.environ.get("SPLOTCH_CHECKED") == "1" else LIB_PATH)
     if not os.path.exists(p):
         raise RuntimeError(f"CUDA library {p} is missing; run paper_1004_1302_gb300.splotch.build()")
     lib = ctypes.CDLL(p)

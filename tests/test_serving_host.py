@@ -39,3 +39,94 @@ def test_poisson_arrivals_are_increasing_and_seeded():
     b = [r.arrival for r in serve.poisson_arrivals(reqs2, rate=10.0, seed=3)]
     assert a == b and all(x < y for x, y in zip(a, a[1:]))
     assert 2.0 < a[-1] < 10.0     # 50 arrivals at 10/s
+
+
+# --- watchdog and cancellation, with the device replaced by fakes -------------
+
+class _Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 0.001          # every reading advances the clock by 1 ms
+        return self.t
+
+
+class _Event:
+    def __init__(self, clock, end):
+        self.clock, self.end = clock, end
+
+    def query(self):
+        return self.clock.t >= self.end
+
+
+class _Info:
+    status, tile_entries = S.OK, 0
+
+
+class _FakeFrame:
+    def info(self, stream=None):
+        return _Info()
+
+
+class _FakeServer(serve.RenderServer):
+    """The request loop over a device that takes `work[rid]` seconds per
+    request (inf: never ends)."""
+
+    def __init__(self, clock, work, max_inflight=2, timeout=None):
+        self.request_timeout_s = timeout
+        self._cancel, self._cancel_lock = set(), __import__("threading").Lock()
+        self.budget, self.in_use, self.peak_in_use = 10_000, 0, 0
+        self.keep_images = False
+        self.slots = [serve._Slot(None, None, None) for _ in range(max_inflight)]
+        self.clock, self.work = clock, work
+
+    def count(self, req):
+        return 100
+
+    def _cap(self, req):
+        return 1000
+
+    def _bytes(self, req, cap):
+        return 1000
+
+    def _launch(self, slot, req, cap):
+        slot.req, slot.frame = req, _FakeFrame()
+        slot.event = _Event(self.clock, self.clock.t + self.work[req.rid])
+        return True
+
+
+def _reqs(n, gap=0.0):
+    return [serve.Request(k, (0, 0, 0, 1, 1, 1), None, 0, arrival=k * gap) for k in range(n)]
+
+
+def test_watchdog_reports_a_stuck_request_and_keeps_its_slot():
+    clk = _Clock()
+    srv = _FakeServer(clk, {0: float("inf"), 1: 0.01, 2: 0.01, 3: 0.01}, max_inflight=2, timeout=0.05)
+    done, st = srv.serve(_reqs(4), clock=clk, idle_sleep=0.0)
+    by = {r.rid: r for r in done}
+    assert by[0].status == S.ERR_TIMEOUT and 0.05 < by[0].done - by[0].admitted < 0.06
+    assert all(by[k].status == S.OK for k in (1, 2, 3))
+    assert st["timed_out"] == 1 and st["completed"] == 3
+    # the stuck request still holds its slot and memory until its work ends
+    stuck = [s for s in srv.slots if s.req is not None]
+    assert len(stuck) == 1 and stuck[0].quarantined and srv.in_use == 1000
+    srv.work = {}
+    stuck[0].event.end = 0.0                 # the device work finally ends
+    srv.serve([], clock=clk, idle_sleep=0.0)
+    assert srv.in_use == 0 and all(s.req is None for s in srv.slots)
+
+
+def test_cancellation_of_waiting_and_running_requests():
+    clk = _Clock()
+    reqs = _reqs(5)
+    reqs[1].cancel_after = 0.0                # cancelled before it starts (one slot, request 0 runs)
+    reqs[0].cancel_after = 0.02               # cancelled while it runs
+    srv = _FakeServer(clk, {k: 0.05 for k in range(5)}, max_inflight=1)
+    srv.cancel(3)
+    done, st = srv.serve(reqs, clock=clk, idle_sleep=0.0)
+    by = {r.rid: r for r in done}
+    assert by[0].status == serve.CANCELLED and by[1].status == serve.CANCELLED and by[3].status == serve.CANCELLED
+    assert by[2].status == S.OK and by[4].status == S.OK
+    assert by[1].admitted is None and by[3].admitted is None
+    assert st["cancelled"] == 3 and st["completed"] == 2 and srv.in_use == 0
