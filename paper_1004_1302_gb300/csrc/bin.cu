@@ -3,17 +3,19 @@
 // 1. Every visible particle, in render order, adds one entry (super-tile,
 //    particle) per super-tile (8 x 8 screen tiles) its box meets; offsets come
 //    from a scan of the per-particle counts, so entries sit at fixed places.
-//    The entries of particles touching more super-tiles than a threshold are
-//    shared out over the whole CTA (the "split particles" idea of Section 3.2
-//    applied to the emission of work items).
-// 2. One stable radix pass groups the entries by super-tile, keeping render
-//    order inside each group.
-// 3. Each super-tile's list is cut into units of kUnit entries.  A particle's
-//    footprint inside its super-tile is a rectangle of its 8 x 8 fine tiles;
-//    per unit the fine-tile counts come from a 2-D difference array, a scan
-//    over units and over fine tiles gives every (unit, fine tile) its output
-//    position, and row and column ballots over each warp's entries give every
-//    (entry, fine tile) its rank inside the tile.
+//    The count pass gathers each particle's box once and stores it (in tiles)
+//    in list order, so the emission reads it sequentially.  The entries of
+//    particles touching more super-tiles than a threshold are shared out over
+//    the whole CTA (the "split particles" idea of Section 3.2 applied to the
+//    emission of work items).  An entry's key holds the super-tile id and,
+//    above it, the rectangle of fine tiles the particle meets there.
+// 2. One stable radix pass over the id bits groups the entries by super-tile,
+//    keeping render order inside each group.
+// 3. Each super-tile's list is cut into units of kUnit entries.  Per unit the
+//    fine-tile counts come from a 2-D difference array over the rectangles, a
+//    scan over units and over fine tiles gives every (unit, fine tile) its
+//    output position, and row and column ballots over each warp's entries give
+//    every (entry, fine tile) its rank inside the tile.
 //    The result is, for every fine tile (row-major), the particles whose box
 //    meets it in render order: bit-exact, as a stable sort by tile would give.
 #include "internal.h"
@@ -23,7 +25,22 @@ namespace spl {
 
 constexpr int kBinStep = 2048;   // particles per CTA step of the emission kernel
 
-// Number of (super-)tiles of side 2^shift pixels that a pixel box meets.
+constexpr int kSuperShift = 3;   // log2 of kSuperSide
+
+// Fine-tile rectangle code of an entry key: columns c0..c1 and rows r0..r1 of
+// the tile box t inside super-tile (sx, sy).
+__device__ __forceinline__ uint32_t rect_code(const ushort4 t, int sx, int sy) {
+    const int ox = sx << kSuperShift, oy = sy << kSuperShift;
+    const uint32_t c0 = (uint32_t)max((int)t.x - ox, 0), c1 = (uint32_t)min((int)t.z - ox, kSuperSide - 1);
+    const uint32_t r0 = (uint32_t)max((int)t.y - oy, 0), r1 = (uint32_t)min((int)t.w - oy, kSuperSide - 1);
+    return c0 | (c1 << 3) | (r0 << 6) | (r1 << 9);
+}
+
+__device__ __forceinline__ uint32_t entry_key(const ushort4 t, int sx, int sy, int nsx) {
+    return (uint32_t)(sy * nsx + sx) | (rect_code(t, sx, sy) << kSidBits);
+}
+
+// Number of (super-)tiles of side 2^shift units that a box meets.
 __device__ __forceinline__ uint32_t cells_of(const ushort4 b, int shift) {
     return (uint32_t)((b.z >> shift) - (b.x >> shift) + 1) * (uint32_t)((b.w >> shift) - (b.y >> shift) + 1);
 }
@@ -46,7 +63,14 @@ __global__ void __launch_bounds__(256) k_bin_reduce(BinArgs a) {
     unsigned long long sum = 0;
     for (uint64_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
         const uint32_t p = list[k];
-        if (SPL_CHECK(a.hdr, p < a.hdr->layout.n)) sum += cells_of(a.box[p], a.sshift);
+        ushort4 t = make_ushort4(1, 1, 0, 0);
+        if (SPL_CHECK(a.hdr, p < a.hdr->layout.n)) {
+            // the particle's box in tiles, stored in list order for the emission
+            const ushort4 b = a.box[p];
+            t = make_ushort4(b.x >> a.tshift, b.y >> a.tshift, b.z >> a.tshift, b.w >> a.tshift);
+            sum += cells_of(t, kSuperShift);
+        }
+        a.sbox[k] = t;
     }
     unsigned long long tot;
     block_exclusive_scan64<256>(sum, ws, &tot);
@@ -97,7 +121,7 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
     __shared__ uint32_t s_lp[kBinStep];       // large particles, per warp segment of 256, in list order
     __shared__ uint32_t s_loff[kBinStep];     // their first entry within the warp's run
     __shared__ uint32_t s_lcell[kBinStep];    // their first cell among the warp's large cells
-    __shared__ ushort4 s_lbox[kBinStep];      // their super-tile boxes
+    __shared__ ushort4 s_lbox[kBinStep];      // their boxes in tiles
     __shared__ uint32_t s_wtot[3][8];         // per warp: cells, large particles, large cells
     const uint32_t n = a.hdr->visible;
     const uint32_t *list = a.hdr->sorted_buf ? a.list[1] : a.list[0];
@@ -110,7 +134,7 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
     for (uint64_t step = beg; step < end; step += kBinStep) {
         const uint32_t m = (uint32_t)min((uint64_t)kBinStep, end - step);
         uint32_t p[kRounds], off[kRounds];
-        ushort4 tb[kRounds];
+        ushort4 tb[kRounds];                  // box in tiles; (1, 1, 0, 0): no entries
         uint32_t cells = 0, nl = 0, lcells = 0;
 #pragma unroll
         for (int q = 0; q < kRounds; ++q) {
@@ -120,11 +144,8 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
             tb[q] = make_ushort4(1, 1, 0, 0);
             if (j < m) {
                 p[q] = list[step + j];
-                if (SPL_CHECK(a.hdr, p[q] < a.hdr->layout.n)) {
-                    const ushort4 b = a.box[p[q]];
-                    tb[q] = make_ushort4(b.x >> a.sshift, b.y >> a.sshift, b.z >> a.sshift, b.w >> a.sshift);
-                    nt = (uint32_t)(tb[q].z - tb[q].x + 1) * (uint32_t)(tb[q].w - tb[q].y + 1);
-                }
+                tb[q] = a.sbox[step + j];
+                if (tb[q].x <= tb[q].z) nt = cells_of(tb[q], kSuperShift);
             }
             const bool big = nt > a.large_tiles;
             const uint32_t inc = warp_inclusive_scan(nt);
@@ -167,12 +188,13 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
         // small particles: the owner writes its entries
 #pragma unroll
         for (int q = 0; q < kRounds; ++q) {
-            const ushort4 b = tb[q];
+            const ushort4 t = tb[q];
+            if (t.x > t.z) continue;
             unsigned long long e = running + base + off[q];
-            for (int ty = b.y; ty <= b.w; ++ty)
-                for (int tx = b.x; tx <= b.z; ++tx, ++e)
+            for (int sy = t.y >> kSuperShift; sy <= (t.w >> kSuperShift); ++sy)
+                for (int sx = t.x >> kSuperShift; sx <= (t.z >> kSuperShift); ++sx, ++e)
                     if (e < a.cap) {
-                        a.ek[e] = (uint32_t)(ty * a.nsx + tx);
+                        a.ek[e] = entry_key(t, sx, sy, a.nsx);
                         a.ev[e] = p[q];
                     }
         }
@@ -197,12 +219,13 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
             }
             const uint32_t i = seg * 256u + lo;
             const uint32_t k = cl - lc[lo];
-            const ushort4 b = s_lbox[i];
-            const uint32_t w = (uint32_t)(b.z - b.x + 1);
+            const ushort4 t = s_lbox[i];
+            const int sx0 = t.x >> kSuperShift, sy0 = t.y >> kSuperShift;
+            const uint32_t w = (uint32_t)((t.z >> kSuperShift) - sx0 + 1);
             const uint32_t row = k / w, col = k - row * w;
             const unsigned long long e = running + cbase + s_loff[i] + k;
             if (e < a.cap) {
-                a.ek[e] = (uint32_t)((b.y + row) * a.nsx + b.x + col);
+                a.ek[e] = entry_key(t, sx0 + (int)col, sy0 + (int)row, a.nsx);
                 a.ev[e] = s_lp[i];
             }
         }
@@ -213,8 +236,8 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
     if (threadIdx.x == 0 && nlarge_cta) atomicAdd(&a.hdr->n_large, nlarge_cta);
 }
 
-// Offsets of groups in a sequence sorted by group id: offsets[g] = first
-// entry of group g, offsets[ngroups] = n.
+// Offsets of groups in a sequence sorted by group id (the key's low kSidBits
+// bits): offsets[g] = first entry of group g, offsets[ngroups] = n.
 __global__ void __launch_bounds__(256) k_group_offsets(const uint32_t *count, const uint32_t *ids, uint32_t *off,
                                                        uint32_t ngroups) {
     const uint32_t n = *count;
@@ -224,26 +247,26 @@ __global__ void __launch_bounds__(256) k_group_offsets(const uint32_t *count, co
         return;
     }
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-        const uint32_t t = ids[e];
-        const uint32_t prev = e ? ids[e - 1] + 1u : 0u;
+        const uint32_t t = ids[e] & kSidMask;
+        const uint32_t prev = e ? (ids[e - 1] & kSidMask) + 1u : 0u;
         for (uint32_t tt = prev; tt <= t; ++tt) off[tt] = e;
         if (e == n - 1)
             for (uint32_t tt = t + 1; tt <= ngroups; ++tt) off[tt] = n;
     }
 }
 
-// Fine-tile rectangle (columns c0..c1, rows r0..r1, in 0..7) that a
-// particle's pixel box meets inside the super-tile whose first fine tile is
-// (ox, oy).
+// Fine-tile rectangle (columns c0..c1, rows r0..r1, in 0..7) of an entry,
+// from its key.
 struct FineRect {
     int c0, c1, r0, r1;
 };
-__device__ __forceinline__ FineRect fine_rect(const ushort4 b, int tshift, int ox, int oy) {
+__device__ __forceinline__ FineRect key_rect(uint32_t key) {
+    const uint32_t r = key >> kSidBits;
     FineRect f;
-    f.c0 = max((b.x >> tshift) - ox, 0);
-    f.c1 = min((b.z >> tshift) - ox, kSuperSide - 1);
-    f.r0 = max((b.y >> tshift) - oy, 0);
-    f.r1 = min((b.w >> tshift) - oy, kSuperSide - 1);
+    f.c0 = (int)(r & 7u);
+    f.c1 = (int)((r >> 3) & 7u);
+    f.r0 = (int)((r >> 6) & 7u);
+    f.r1 = (int)((r >> 9) & 7u);
     return f;
 }
 
@@ -283,13 +306,10 @@ __global__ void __launch_bounds__(256) k_fine_count(FineArgs a) {
     const uint32_t u = blockIdx.x;
     if (u >= a.hdr->n_units) return;
     const uint4 un = a.units[u];
-    const int ox = (int)(un.x % a.nsx) * kSuperSide, oy = (int)(un.x / a.nsx) * kSuperSide;
     if (threadIdx.x < (kSuperSide + 1) * (kSuperSide + 1)) (&diff[0][0])[threadIdx.x] = 0;
     __syncthreads();
     for (uint32_t i = un.y + threadIdx.x; i < un.z; i += 256) {
-        const uint32_t p = a.sval[i];
-        if (!SPL_CHECK(a.hdr, p < a.hdr->layout.n)) continue;
-        const FineRect f = fine_rect(a.box[p], a.tshift, ox, oy);
+        const FineRect f = key_rect(a.skey[i]);
         atomicAdd(&diff[f.r0][f.c0], 1);
         atomicAdd(&diff[f.r0][f.c1 + 1], -1);
         atomicAdd(&diff[f.r1 + 1][f.c0], -1);
@@ -423,7 +443,7 @@ __global__ void __launch_bounds__(256) k_fine_emit(FineArgs a) {
         FineRect f{1, 0, 1, 0};                      // empty
         if (i < un.z) {
             p = a.sval[i];
-            if (SPL_CHECK(a.hdr, p < a.hdr->layout.n)) f = fine_rect(a.box[p], a.tshift, ox, oy);
+            f = key_rect(a.skey[i]);
         }
         const uint32_t rows = f.r0 <= f.r1 ? (0xFFu >> (kSuperSide - 1 - f.r1)) & (0xFFu << f.r0) : 0u;
         const uint32_t cols = f.c0 <= f.c1 ? (0xFFu >> (kSuperSide - 1 - f.c1)) & (0xFFu << f.c0) : 0u;
@@ -509,11 +529,14 @@ static int sm_count_bin() {
     return v > 0 ? v : 148;
 }
 
-int super_passes(uint32_t nsuper) {
+// Bits of a super-tile id (at most kSidBits) and the 8-bit passes that sort them.
+static int super_bits(uint32_t nsuper) {
     int bits = 0;
-    while (bits < 32 && (1ull << bits) < (unsigned long long)nsuper) ++bits;
-    return (bits + 7) / 8;
+    while (bits < kSidBits && (1ull << bits) < (unsigned long long)nsuper) ++bits;
+    return bits;
 }
+
+int super_passes(uint32_t nsuper) { return (super_bits(nsuper) + 7) / 8; }
 
 uint64_t fine_list_offset(const Layout &L) { return L.off_ek[1 - (super_passes(L.nsuper) & 1)]; }
 
@@ -525,6 +548,8 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     a.list[0] = at<uint32_t>(ws, L.off_sv[0]);
     a.list[1] = at<uint32_t>(ws, L.off_sv[1]);
     a.box = at<ushort4>(ws, L.off_box);
+    a.sbox = at<ushort4>(ws, L.off_sbox);
+    a.tshift = tshift;
     a.part = at<uint64_t>(ws, L.off_part);
     a.ctas = L.sort_ctas;
     a.ek = at<uint32_t>(ws, L.off_ek[0]);
@@ -556,7 +581,9 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
         p.key_out = at<uint32_t>(ws, L.off_ek[(pass + 1) & 1]);
         p.val_out = at<uint32_t>(ws, L.off_ev[(pass + 1) & 1]);
         p.shift = 8u * pass;
-        p.mask = 0xFFu;
+        // only the super-tile id bits: the rectangle code above them is payload
+        const int bits = super_bits(L.nsuper) - 8 * pass;
+        p.mask = bits >= 8 ? 0xFFu : (1u << bits) - 1u;
         e = launch_radix_pass(p, st);
         if (e != cudaSuccess) return e;
     }

@@ -31,7 +31,7 @@ struct Layout {
     uint32_t ent_ctas;       // CTAs of a radix pass over tile entries
     uint32_t hist_ctas;      // max(sort_ctas, ent_ctas): rows of the histogram table
     uint32_t pad0;
-    uint64_t off_geo, off_col, off_key, off_box;   // geo: {sx, sy, r2, -log2(e)/sigma_pix^2}; col: {Er, Eg, Eb, A}
+    uint64_t off_geo, off_col, off_key, off_box, off_sbox;   // geo: {sx, sy, r2, -log2(e)/sigma_pix^2}; col: {Er, Eg, Eb, A}
     uint64_t off_sk[2], off_sv[2];
     uint64_t off_part;
     uint64_t off_hist, off_htot;
@@ -136,10 +136,19 @@ struct RadixPass {
 };
 
 // Emission of (super-tile, particle) entries in render order.
+// A (super-tile, particle) entry key: the super-tile id in the low kSidBits
+// bits (the only bits the grouping pass sorts on) and, above them, the
+// particle's rectangle of fine tiles inside that super-tile (c0, c1, r0, r1,
+// 3 bits each), so the fine expansion needs no gather of the particle's box.
+constexpr int kSidBits = 20;
+constexpr uint32_t kSidMask = (1u << kSidBits) - 1u;
+
 struct BinArgs {
     Header *hdr;
     const uint32_t *list[2];   // ordered visible list candidates (sorted_buf selects)
     const ushort4 *box;
+    ushort4 *sbox;             // tile-level box per ordered position (written by the reduce, read by the emission)
+    int tshift;                // log2(tile side)
     uint64_t *part;            // per-CTA partial sums
     uint32_t ctas;
     uint32_t *ek, *ev;         // emitted entries (super-tile id, particle)

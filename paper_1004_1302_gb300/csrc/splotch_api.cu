@@ -50,6 +50,7 @@ int compute_layout(uint64_t n, int width, int height, int tile, uint64_t cap, La
     L.off_col = take(n * 16);
     L.off_key = take(n * 4);
     L.off_box = take(n * 8);
+    L.off_sbox = take(n * 8);
     for (int b = 0; b < 2; ++b) {
         L.off_sk[b] = take(n * 4);
         L.off_sv[b] = take(n * 4);
