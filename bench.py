@@ -533,10 +533,11 @@ def run_serving(args, dev):
                  max_tile_entries=int(2.2 * res.n))
     fr.render()
     med, mean = time_frames(fr, 3, 1, torch.cuda.current_stream(dev))
+    stages = stage_times(fr, 3, 1, torch.cuda.current_stream(dev))
     inf = fr.info()
     out["full_frame"] = {"particles": res.n, "ms": mean, "p50_ms": med, "value": res.n / (mean * 1e-3),
                          "visible": int(inf.visible), "tile_entries": int(inf.tile_entries),
-                         "workspace_bytes": int(fr.ws_bytes), "status": int(inf.status)}
+                         "workspace_bytes": int(fr.ws_bytes), "status": int(inf.status), "stages_ms": stages}
     del fr
     torch.cuda.empty_cache()
     # request stream

@@ -61,16 +61,32 @@ __global__ void __launch_bounds__(256) k_bin_reduce(BinArgs a) {
     uint64_t beg, end;
     bin_range(a.ctas, n, &beg, &end);
     unsigned long long sum = 0;
-    for (uint64_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
-        const uint32_t p = list[k];
-        ushort4 t = make_ushort4(1, 1, 0, 0);
-        if (SPL_CHECK(a.hdr, p < a.hdr->layout.n)) {
-            // the particle's box in tiles, stored in list order for the emission
-            const ushort4 b = a.box[p];
-            t = make_ushort4(b.x >> a.tshift, b.y >> a.tshift, b.z >> a.tshift, b.w >> a.tshift);
-            sum += cells_of(t, kSuperShift);
+    // eight independent gathers in flight per thread (the boxes are read in
+    // render order, i.e. at random)
+    constexpr int kIlp = 8;
+    for (uint64_t k0 = beg; k0 < end; k0 += (uint64_t)kIlp * blockDim.x) {
+        uint32_t p[kIlp];
+        ushort4 b[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            const uint64_t k = k0 + (uint64_t)u * blockDim.x + threadIdx.x;
+            p[u] = k < end ? list[k] : 0xFFFFFFFFu;
         }
-        a.sbox[k] = t;
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u)
+            b[u] = p[u] != 0xFFFFFFFFu && SPL_CHECK(a.hdr, p[u] < a.hdr->layout.n) ? a.box[p[u]]
+                                                                                   : make_ushort4(1, 1, 0, 0);
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            const uint64_t k = k0 + (uint64_t)u * blockDim.x + threadIdx.x;
+            if (k >= end) continue;
+            // the particle's box in tiles, stored in list order for the emission
+            const ushort4 t = b[u].x > b[u].z ? make_ushort4(1, 1, 0, 0)
+                                              : make_ushort4(b[u].x >> a.tshift, b[u].y >> a.tshift,
+                                                             b[u].z >> a.tshift, b[u].w >> a.tshift);
+            if (t.x <= t.z) sum += cells_of(t, kSuperShift);
+            a.sbox[k] = t;
+        }
     }
     unsigned long long tot;
     block_exclusive_scan64<256>(sum, ws, &tot);
