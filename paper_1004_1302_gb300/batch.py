@@ -21,7 +21,7 @@ class BatchRenderer:
     keys plus an optional per-frame `large_threshold_px`."""
 
     def __init__(self, jobs, tile: int = 16, batch: int = 128, large_threshold_px: int = 0, streams: int = 4,
-                 device="cuda"):
+                 groups: int = 1, device="cuda"):
         import torch
         if not 0 < len(jobs) <= S.MAX_BATCH:
             raise ValueError(f"a batch holds 1..{S.MAX_BATCH} frames")
@@ -37,7 +37,8 @@ class BatchRenderer:
                 (dp, cam, pal, mode), thr = job, large_threshold_px
             self.frames.append(S.Frame(dp, cam, pal, mode, tile=tile, batch=batch, large_threshold_px=thr,
                                        device=self.device))
-        self.counter = torch.zeros(4, dtype=torch.int32, device=self.device)
+        self.groups = max(0, min(int(groups), len(self.frames)))
+        self.counter = torch.zeros(4 * len(self.frames), dtype=torch.int32, device=self.device)   # 16 B per group
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(max(1, streams))]
         self.graph = None
         self._items = None
@@ -71,21 +72,37 @@ class BatchRenderer:
         return self._items
 
     def enqueue(self):
-        """Enqueue one batch on the current stream (capturable)."""
+        """Enqueue one batch on the current stream (capturable).  With
+        `groups` > 1 the frames are cut into that many consecutive groups; the
+        render of a group waits for that group's preparation only, so the
+        preparation of the next groups runs meanwhile."""
         torch = self.torch
         main = torch.cuda.current_stream(self.device)
         for s in self.streams:
             s.wait_stream(main)
-        for k, f in enumerate(self.frames):
-            s = self.streams[k % len(self.streams)]
-            f.transform(s)
-            f.colorize(s)
-            f.sort(s)
-            f.bin(s)
-        for s in self.streams:
-            main.wait_stream(s)
-        S.splotch_render_tiles_batch(self._batch_items(), self.tile, self.batch, self.counter.data_ptr(),
-                                     main.cuda_stream)
+        if self.groups == 0:
+            # whole frames (per-tile render, no persistent kernel) spread over the streams
+            for k, f in enumerate(self.frames):
+                f.run(self.streams[k % len(self.streams)])
+            for s in self.streams:
+                main.wait_stream(s)
+            return
+        items = self._batch_items()
+        n, G = len(self.frames), self.groups
+        bounds = [round(g * n / G) for g in range(G + 1)]
+        k = 0
+        for g in range(G):
+            for f in self.frames[bounds[g]:bounds[g + 1]]:
+                s = self.streams[k % len(self.streams)]
+                k += 1
+                f.transform(s)
+                f.colorize(s)
+                f.sort(s)
+                f.bin(s)
+            for s in self.streams:
+                main.wait_stream(s)
+            S.splotch_render_tiles_batch(items[bounds[g]:bounds[g + 1]], self.tile, self.batch,
+                                         self.counter.data_ptr() + 16 * g, main.cuda_stream)
 
     def capture(self):
         """Capture one batch into a CUDA graph (after prepare())."""
