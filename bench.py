@@ -26,9 +26,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "config1: 10M particles, gas 6M (1000 Plummer spheres + 20% uniform) and dark matter 4M, 1920x1080, absorptive"
+WORKLOAD = "two-species set: 10M particles, gas 6M (1000 Plummer spheres + 20% uniform) and dark matter 4M, 1920x1080, absorptive"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
-RENDER_PROFILE = os.path.join(ROOT, "profiles", "k_render_config1_1080p_absorptive.txt")
+RENDER_PROFILE = os.path.join(ROOT, "profiles", "k_render_two_species_10m_1080p_absorptive.txt")
 
 
 def parse():
@@ -145,7 +145,7 @@ def run_reference(args, world, rank):
     import synth
     from oracle import oracle as O
     O.build()
-    ps, cam = synth.config1()
+    ps, cam = synth.two_species()
     step = 16
     sub = ps.subsample(step)
     pal = synth.colormap()
@@ -236,7 +236,7 @@ def run_split(args, dev):
     rows = []
     for n in TABLE2_SIZES:
         n_gas = int(round(0.6 * n))
-        ps, cam = synth.config1(n_gas=n_gas, n_dm=n - n_gas)
+        ps, cam = synth.two_species(n_gas=n_gas, n_dm=n - n_gas)
         dp = S.upload(ps, dev, "f32")
         res = {"particles": n}
         imgs = {}
@@ -263,7 +263,7 @@ def run_split(args, dev):
         torch.cuda.empty_cache()
     return {"form": "split", "metric": "display time per frame, split vs no split (1920x1080, absorptive)",
             "unit": "ms", "higher_is_better": False,
-            "config": {"workload": "config1 generator at the set sizes of the paper's Table 2 (60% gas, 40% dark "
+            "config": {"workload": "two-species generator at the set sizes of the paper's Table 2 (60% gas, 40% dark "
                                    "matter), 1920x1080, absorptive", "tile": args.tile, "batch": args.batch},
             "sets": rows}
 
@@ -287,7 +287,7 @@ def run_io(args, dev):
     pal = synth.colormap()
     snaps, paths = [], []
     for k in range(K):
-        ps, cam = synth.config1(seed=synth.SEED + k)
+        ps, cam = synth.two_species(seed=synth.SEED + k)
         snaps.append(ps)
         paths.append(os.path.join(tmp, f"snap{k}.bin"))
         synth.write_block_file(paths[-1], [ps.x, ps.y, ps.z, ps.h, ps.v])
@@ -359,7 +359,7 @@ def run_io(args, dev):
     file_bytes = 5 * 4 * n
     return {"form": "io", "metric": "frames/s with the read stage (1920x1080, absorptive)", "unit": "frames/s",
             "higher_is_better": True,
-            "config": {"workload": f"{K} snapshots of config1 (10M particles) as block files, 5 blocks x 10M "
+            "config": {"workload": f"{K} snapshots of the 10M two-species set as block files, 5 blocks x 10M "
                                    "float32 (200 MB each), page-cache reads", "tile": args.tile,
                        "batch": args.batch, "chunk_bytes": 32 << 20},
             "load_GBps": K * file_bytes / t_load / 1e9, "load_ms_per_snapshot": 1e3 * t_load / K,
@@ -379,11 +379,11 @@ def run_precision(args, dev):
     import synth
     from oracle import oracle as O
     from paper_1004_1302_gb300 import splotch as S
-    ps, cam = synth.config2()
+    ps, cam = synth.clustered()
     pal = synth.colormap()
     stream = torch.cuda.current_stream(dev)
     out = {"form": "precision", "metric": "particles rendered/s (1920x1080, absorptive)", "unit": "particles/s",
-           "config": {"workload": "config2: 100M particles, 5000 Plummer spheres + 10% uniform, 1920x1080, absorptive",
+           "config": {"workload": "clustered set: 100M particles, 5000 Plummer spheres + 10% uniform, 1920x1080, absorptive",
                       "particles": ps.n}, "dtypes": {}}
     for dtype in ("f32", "f16", "bf16"):
         dp = S.upload(ps, dev, dtype)
@@ -433,7 +433,7 @@ def run_batching(args, dev):
     from paper_1004_1302_gb300 import splotch as S
     from paper_1004_1302_gb300.batch import BatchRenderer
     pal = synth.colormap()
-    ps, _ = synth.config1(width=1024, height=1024)
+    ps, _ = synth.two_species(width=1024, height=1024)
     dp = S.upload(ps, dev, "f32")
     views = [synth.orbit_camera(k, 64, 1024, 1024) for k in range(64)]
     sizes = synth.snapshot_sizes(32)
@@ -480,7 +480,7 @@ def run_batching(args, dev):
     ok = all(st == 0 for st in br.statuses())
     n_frames = len(br.frames)
     return {"form": "batching", "metric": "frames/s and particles rendered/s of the batch", "unit": "particles/s",
-            "config": {"workload": "config3: 64 orbit views of the 10M set at 1024^2 (absorptive) + 32 snapshots "
+            "config": {"workload": "64 orbit views of the 10M two-species set at 1024^2 (absorptive) + 32 snapshots "
                                    "of 10k-2M particles at 512^2 (emission)", "frames": n_frames,
                        "particles": br.particles, "tile": tv["tile"], "batch": tv["batch"],
                        "view_threshold_px": tv["large_threshold_px"], "snapshot_threshold_px": tsn["large_threshold_px"]},
@@ -531,7 +531,7 @@ def run_serving(args, dev):
     t_gen = time.perf_counter() - t0
     pal = synth.colormap()
     out = {"form": "serving", "metric": "requests/s, particles rendered/s and p50/p99 latency", "unit": "particles/s",
-           "config": {"workload": f"config4: {args.lattice}^3 displaced lattice + 10000 Plummer overdensities, "
+           "config": {"workload": f"{args.lattice}^3 displaced lattice + 10000 Plummer overdensities, "
                                   "FP32 pos/h + FP16 intensity, resident", "particles": res.n,
                       "resident_bytes": res.n * 18, "generate_and_upload_s": t_gen}}
     # whole set, one 1920x1080 absorptive frame
@@ -605,7 +605,7 @@ def main():
             print(json.dumps(res), flush=True)
         return
 
-    ps, cam = synth.config1()
+    ps, cam = synth.two_species()
     pal = synth.colormap()
     dp = S.upload(ps, dev, "f32")
     fr = S.Frame(dp, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev)

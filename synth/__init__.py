@@ -6,7 +6,8 @@ same whatever the thread count and whichever slice of it is asked for.  Both
 the FP64 oracle and the CUDA path take their inputs from here; nothing else is
 shared between them.
 
-The workload recipes (the ``config*`` functions) stand in for the paper's
+The workload recipes (``plummer_mixture``, ``two_species``, ``clustered``,
+``snapshot``, ``lattice``) stand in for the paper's
 N-body snapshots (Section 4: a cosmological simulation of 850M particles and
 the Millennium II run), which are not available: clustered Plummer spheres,
 a uniform background, per-particle smoothing lengths and a lognormal scalar.
@@ -184,7 +185,7 @@ def _spheres(set_id: int, n: int, clo: float, chi: float, alo: float, ahi: float
 
 # --- workload recipes -------------------------------------------------------
 
-def config0(n: int = 100_000, seed: int = SEED) -> tuple[ParticleSet, CameraSpec]:
+def plummer_mixture(n: int = 100_000, seed: int = SEED) -> tuple[ParticleSet, CameraSpec]:
     """100k particles in 20 equal Plummer spheres (scale radii U[0.02, 0.1],
     centres U[0.1, 0.9]^3); h ~ LogNormal(ln 0.005, 0.5); intensity ~
     LogNormal(0, 1); one colour-mapped emission species; 256x256 camera."""
@@ -206,7 +207,7 @@ H_MAX_1080 = 200.0 * 1.5 / _S1080
 ETA = 0.02  # density factor of h = eta a (1 + r^2/a^2)^(5/6)
 
 
-def config1(n_gas: int = 6_000_000, n_dm: int = 4_000_000, width=1920, height=1080,
+def two_species(n_gas: int = 6_000_000, n_dm: int = 4_000_000, width=1920, height=1080,
             seed: int = SEED) -> tuple[ParticleSet, CameraSpec]:
     """10M particles in two species.  Gas: 80% in 1000 Plummer spheres with
     scale radii U[0.005, 0.05], 20% uniform background; dark matter: the same
@@ -230,9 +231,9 @@ def config1(n_gas: int = 6_000_000, n_dm: int = 4_000_000, width=1920, height=10
     return ParticleSet(*arrs, species), cam
 
 
-def config2(n: int = 100_000_000, seed: int = SEED) -> tuple[ParticleSet, CameraSpec]:
+def clustered(n: int = 100_000_000, seed: int = SEED) -> tuple[ParticleSet, CameraSpec]:
     """100M particles: 5000 Plummer spheres (scale radii U[0.004, 0.02]) plus
-    10% uniform background; h and intensity drawn as in config0; absorptive
+    10% uniform background; h and intensity drawn as in plummer_mixture; absorptive
     A = 0.1 at 1920x1080.  Intensity is stored reduced-precision by the caller."""
     c, a = _spheres(0x200, 5000, 0.05, 0.95, 0.004, 0.02, seed)
     x, y, z, h, v = _cluster(n, 0x201, c, a, bg_fraction=0.1, h_mode=0, h_mu=math.log(0.005),
@@ -256,8 +257,8 @@ def snapshot_sizes(n_snap: int = 32, lo: float = 1e4, hi: float = 2e6, seed: int
 
 
 def snapshot(k: int, n: int, seed: int = SEED) -> tuple[ParticleSet, CameraSpec]:
-    """Independent snapshot k: the config0 generator with its own key, 512x512."""
-    ps, cam = config0(n=n, seed=(seed + 0x1000 + k) & 0xFFFFFFFF)
+    """Independent snapshot k: the plummer_mixture generator with its own key, 512x512."""
+    ps, cam = plummer_mixture(n=n, seed=(seed + 0x1000 + k) & 0xFFFFFFFF)
     cam = CameraSpec(cam.eye, cam.target, cam.up, cam.fov_x_deg, 512, 512)
     return ps, cam
 

@@ -89,4 +89,4 @@ def image_error(gpu: np.ndarray, ref: np.ndarray) -> np.ndarray:
 def small_two_species(n=100_000, width=320, height=180, seed=synth.SEED):
     """The two-species absorptive recipe at a reduced size (ragged tiles)."""
     n_gas = int(n * 0.6)
-    return synth.config1(n_gas=n_gas, n_dm=n - n_gas, width=width, height=height, seed=seed)
+    return synth.two_species(n_gas=n_gas, n_dm=n - n_gas, width=width, height=height, seed=seed)

@@ -67,7 +67,7 @@ def test_camera_init_rejects_degenerate(S):
 
 def test_workspace_size_and_arguments(S):
     lib = S.load()
-    _, spec = synth.config0(n=10)
+    _, spec = synth.plummer_mixture(n=10)
     cam = S.make_camera(spec)
     p = S.make_params(S.EMISSION, tile=16, batch=128, max_tile_entries=1 << 20)
     small = S.splotch_workspace_size(1000, cam, p)
@@ -84,7 +84,7 @@ def test_workspace_size_and_arguments(S):
 
 def test_calls_reject_bad_workspace_before_launch(S):
     lib = S.load()
-    _, spec = synth.config0(n=10)
+    _, spec = synth.plummer_mixture(n=10)
     cam = S.make_camera(spec)
     p = S.make_params(S.ABSORPTIVE, max_tile_entries=4096)
     parts = S.Particles()

@@ -82,5 +82,5 @@ def test_full_set_frame_matches_oracle_on_sampled_pixels(oracle_mod):
     ref = O.render_frame(sub, cam, pal, O.ABSORPTIVE, tile=16, pixels=pix).image
     got = img[pix[:, 1], pix[:, 0]]
     err = np.abs(got - ref).max(axis=0) / np.abs(ref).max(axis=0)
-    print(f"north-star sampled pixels: {pix.shape[0]}, particles kept {m}, max-abs/max per channel {err}")
+    print(f"full-set frame, sampled pixels: {pix.shape[0]}, particles kept {m}, max-abs/max per channel {err}")
     assert (err <= TOL).all(), err

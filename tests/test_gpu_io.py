@@ -70,7 +70,7 @@ def test_pipeline_images_equal_direct_uploads(tmp_path):
     S.load()
     snaps, paths = [], []
     for k in range(3):
-        ps, cam = synth.config1(n_gas=120_000, n_dm=80_000, width=320, height=200, seed=synth.SEED + k)
+        ps, cam = synth.two_species(n_gas=120_000, n_dm=80_000, width=320, height=200, seed=synth.SEED + k)
         snaps.append(ps)
         paths.append(str(tmp_path / f"snap{k}.bin"))
         synth.write_block_file(paths[-1], [ps.x, ps.y, ps.z, ps.h, ps.v], big_endian=(k % 2 == 1))
@@ -110,7 +110,7 @@ def test_host_pipeline_images_equal_direct_renders():
     import torch
     from paper_1004_1302_gb300 import splotch as S
     S.load()
-    snaps = [synth.config1(n_gas=90_000, n_dm=60_000, width=300, height=180, seed=synth.SEED + k) for k in range(4)]
+    snaps = [synth.two_species(n_gas=90_000, n_dm=60_000, width=300, height=180, seed=synth.SEED + k) for k in range(4)]
     pal = synth.colormap()
     cam = snaps[0][1]
     direct = [S.Frame(S.upload(ps, "cuda", "f32"), cam, pal, S.ABSORPTIVE).render().cpu().numpy() for ps, _ in snaps]

@@ -44,8 +44,8 @@ def _compare_frame(g, o, *, lists=True, image=True, exact_a=True):
     return vis
 
 
-def test_config0_emission_full_size():
-    ps, cam = synth.config0()
+def test_plummer_mixture_100k_emission_full_size():
+    ps, cam = synth.plummer_mixture()
     pal = synth.colormap()
     g = gpu_render(ps, cam, pal, 0)
     o = oracle_render(ps, cam, pal, 0)
@@ -154,11 +154,11 @@ def test_edge_cases():
 
 
 @pytest.mark.slow
-def test_config1_full_size_lists_and_sampled_pixels():
+def test_two_species_10m_full_size_lists_and_sampled_pixels():
     """10M particles, 1920x1080, absorptive, the launch configuration of the
     benchmark: keys, order and tile lists bit-exact; sampled pixels (random,
     three whole rows, and the brightest GPU pixels) within tolerance."""
-    ps, cam = synth.config1()
+    ps, cam = synth.two_species()
     pal = synth.colormap()
     g = gpu_render(ps, cam, pal, 1, tile=16, batch=128)
     rng = np.random.default_rng(7)

@@ -40,7 +40,7 @@ def test_philox_known_answers():
 
 
 def test_generator_slices_agree():
-    ps, _ = synth.config0(n=5000)
+    ps, _ = synth.plummer_mixture(n=5000)
     c, a = synth._spheres(0x0, 20, 0.1, 0.9, 0.02, 0.1)
     tail = synth._cluster(1000, 0x0, c, a, i0=4000, h_mode=0, h_mu=math.log(0.005), h_sigma=0.5)
     np.testing.assert_array_equal(tail[0], ps.x[4000:])
@@ -116,7 +116,7 @@ def test_basis_orthonormal_any_view(oracle_mod):
 
 def test_depth_key_axis_camera_is_z_plus_distance(oracle_mod):
     O = oracle_mod
-    ps, cam = synth.config0(n=20000)
+    ps, cam = synth.plummer_mixture(n=20000)
     geo = O.geometry(cam, ps.x, ps.y, ps.z, ps.h)
     expect = (ps.z.astype(np.float64) + 1.5).astype(np.float32).view(np.uint32)
     vis = geo.visible

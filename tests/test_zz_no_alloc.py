@@ -22,8 +22,8 @@ def test_no_alloc_sort_matches_allocating_sort():
     S.build()
     lib = S.load()
     pal = synth.colormap()
-    cases = [synth.config1(n_gas=120_000, n_dm=80_000, width=640, height=360),
-             synth.config0(n=S.NO_ALLOC_MAX_KEYS)]
+    cases = [synth.two_species(n_gas=120_000, n_dm=80_000, width=640, height=360),
+             synth.plummer_mixture(n=S.NO_ALLOC_MAX_KEYS)]
     for ps, cam in cases:
         dp = S.upload(ps, "cuda", "f32")
         fr = S.Frame(dp, cam, pal, S.ABSORPTIVE)
