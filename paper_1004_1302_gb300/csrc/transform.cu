@@ -134,12 +134,23 @@ __global__ void __launch_bounds__(256) k_transform(TransformArgs a, float4 *geo,
 __global__ void __launch_bounds__(256) k_range(const void *v, int dtype, uint64_t begin, uint64_t end, int use_log,
                                                uint32_t *lo_enc, uint32_t *hi_enc) {
     float lo = INFINITY, hi = -INFINITY;
-    for (uint64_t i = begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < end;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        float u = load_value(v, dtype, i);
-        if (use_log) u = log10f(fmaxf(u, 1e-37f));
-        lo = fminf(lo, u);
-        hi = fmaxf(hi, u);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    // four independent loads in flight per thread
+    for (uint64_t i0 = begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < end; i0 += 4 * stride) {
+        float u[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint64_t i = i0 + k * stride;
+            u[k] = i < end ? load_value(v, dtype, i) : NAN;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k * stride >= end) continue;
+            float w = u[k];
+            if (use_log) w = log10f(fmaxf(w, 1e-37f));
+            lo = fminf(lo, w);
+            hi = fmaxf(hi, w);
+        }
     }
     uint32_t elo = __reduce_min_sync(0xFFFFFFFFu, float_to_ordered(lo));
     uint32_t ehi = __reduce_max_sync(0xFFFFFFFFu, float_to_ordered(hi));
@@ -266,7 +277,7 @@ cudaError_t launch_colorize(const ColorizeArgs &a, void *ws, const Layout &L, cu
         const uint64_t b = a.begin[s], e = a.begin[s + 1];
         if (e <= b || !(isnan(sp.lo) || isnan(sp.hi))) continue;
         uint64_t blocks = (e - b + 255) / 256;
-        int grid = (int)(blocks < (uint64_t)sms * 4 ? blocks : (uint64_t)sms * 4);
+        int grid = (int)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);
         k_range<<<grid, 256, 0, st>>>(a.v, a.dtype, b, e, sp.use_log, &header(ws)->range_lo_enc[s],
                                        &header(ws)->range_hi_enc[s]);
         count_launches(1);
