@@ -539,6 +539,13 @@ def run_serving(args, dev):
     fr = S.Frame(res, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev,
                  max_tile_entries=int(2.2 * res.n))
     fr.render()
+    if args.frames_only:             # whole-set frames only (for profilers)
+        for _ in range(args.frames_only):
+            fr.run()
+        torch.cuda.synchronize(dev)
+        inf = fr.info()
+        return {"form": "serving", "frames": args.frames_only, "status": int(inf.status),
+                "tile_entries": int(inf.tile_entries)}
     med, mean = time_frames(fr, 3, 1, torch.cuda.current_stream(dev))
     stages = stage_times(fr, 3, 1, torch.cuda.current_stream(dev))
     inf = fr.info()
