@@ -53,6 +53,24 @@ def parse():
     return ap.parse_args()
 
 
+def slowest_rank_ms(ms: float, world: int, device=None) -> float:
+    """The timed region's duration across ranks: the slowest rank's (weak
+    scaling: every rank renders its own frames, the job ends with the last)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(particles_per_rank: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job particles/s: every rank renders `particles_per_rank` per
+    step, the job takes the slowest rank's `ms`."""
+    return world * particles_per_rank * steps / (ms * 1e-3)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -660,10 +678,7 @@ def main():
         barrier()
     launches = S.splotch_launch_count() - launches0
     total_ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = slowest_rank_ms(total_ms, world, dev)
     frame_ms = sorted(e[0].elapsed_time(e[4]) for e in ev)
     stage = {
         "transform_colorize": float(np.mean([e[0].elapsed_time(e[1]) for e in ev])),
@@ -672,7 +687,7 @@ def main():
         "render": float(np.mean([e[3].elapsed_time(e[4]) for e in ev])),
     }
     ms_per_step = total_ms / K
-    value = world * ps.n * K / (total_ms * 1e-3)
+    value = job_throughput(ps.n, K, world, total_ms)
     final_status = fr.info().status
     F = fr.fragments()
     clk = clocks.summary()
@@ -764,11 +779,8 @@ def main():
         torch.cuda.synchronize(dev)
         e2e_status = int(pipe.info(0).status)
         e2e_ms = a.elapsed_time(b) / K
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        out["e2e"] = {"value": world * ps.n / (e2e_ms * 1e-3), "unit": "particles/s",
+        e2e_ms = slowest_rank_ms(e2e_ms, world, dev)
+        out["e2e"] = {"value": job_throughput(ps.n, 1, world, e2e_ms), "unit": "particles/s",
                       "h2d_bytes_per_step": int(sum(h.numel() * h.element_size() for h in host)),
                       "d2h_bytes_per_step": int(img_host.numel() * 4), "ms_per_step": e2e_ms,
                       "pipelined": "the input copy of step k + 1 and the image read-back of step k - 1 overlap the "
