@@ -123,9 +123,11 @@ __global__ void __launch_bounds__(1024) k_bin_scan(BinArgs a) {
 }
 
 // Each CTA walks its range in steps of kBinStep particles (list order); warp
-// w takes the step's w-th run of 256 particles, 32 at a time, and keeps them in
-// registers.  Warp scans give each particle its first entry within the warp's
-// run, a scan of the 8 warp totals places the runs.  A particle meeting at
+// w takes the step's w-th run of 256 particles, lane l the run's particles
+// 8 l .. 8 l + 7, kept in registers.  A lane sums its own particles; one warp
+// scan of (cells, large cells) and one of the large count give each particle
+// its first entry within the warp's run, a scan of the 8 warp totals places
+// the runs.  A particle meeting at
 // most `large_tiles` super-tiles is written by its own lane.  The larger ones
 // go to the warp's segment of shared memory; their cells are laid end to end
 // (warp by warp, list order) and dealt to all threads of the CTA, one cell per
@@ -142,7 +144,6 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
     const uint32_t n = a.hdr->visible;
     const uint32_t *list = a.hdr->sorted_buf ? a.list[1] : a.list[0];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt = lanemask_lt();
     uint64_t beg, end;
     bin_range(a.ctas, n, &beg, &end);
     unsigned long long running = a.part[blockIdx.x];
@@ -151,34 +152,47 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
         const uint32_t m = (uint32_t)min((uint64_t)kBinStep, end - step);
         uint32_t p[kRounds], off[kRounds];
         ushort4 tb[kRounds];                  // box in tiles; (1, 1, 0, 0): no entries
-        uint32_t cells = 0, nl = 0, lcells = 0;
+        // lane l owns the warp run's items 8 l .. 8 l + 7 (consecutive in list order)
+        uint32_t nt[kRounds];
+        uint32_t my_cells = 0, my_lcells = 0, my_nl = 0;
 #pragma unroll
         for (int q = 0; q < kRounds; ++q) {
-            const uint32_t j = warp * 256u + 32u * q + lane;
-            uint32_t nt = 0;
+            const uint32_t j = warp * 256u + lane * kRounds + q;
+            nt[q] = 0;
             p[q] = 0;
             tb[q] = make_ushort4(1, 1, 0, 0);
             if (j < m) {
                 p[q] = list[step + j];
                 tb[q] = a.sbox[step + j];
-                if (tb[q].x <= tb[q].z) nt = cells_of(tb[q], kSuperShift);
+                if (tb[q].x <= tb[q].z) nt[q] = cells_of(tb[q], kSuperShift);
             }
-            const bool big = nt > a.large_tiles;
-            const uint32_t inc = warp_inclusive_scan(nt);
-            const uint32_t linc = warp_inclusive_scan(big ? nt : 0u);
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, big);
-            off[q] = cells + inc - nt;
-            if (big) {
-                const uint32_t r = warp * 256u + nl + __popc(bal & lt);
+            const bool big = nt[q] > a.large_tiles;
+            my_cells += nt[q];
+            my_lcells += big ? nt[q] : 0u;
+            my_nl += big ? 1u : 0u;
+        }
+        // one scan of (cells, large cells) and one of the large count place the lane's items in the run
+        const unsigned long long inc2 =
+            warp_inclusive_scan64((unsigned long long)my_cells | ((unsigned long long)my_lcells << 32));
+        const uint32_t incl = warp_inclusive_scan(my_nl);
+        const unsigned long long tot2 = __shfl_sync(0xFFFFFFFFu, inc2, 31);
+        const uint32_t cells = (uint32_t)tot2, lcells = (uint32_t)(tot2 >> 32);
+        const uint32_t nl = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        uint32_t o = (uint32_t)inc2 - my_cells, lo_cell = (uint32_t)(inc2 >> 32) - my_lcells, lr = incl - my_nl;
+#pragma unroll
+        for (int q = 0; q < kRounds; ++q) {
+            off[q] = o;
+            if (nt[q] > a.large_tiles) {
+                const uint32_t r = warp * 256u + lr;
                 s_lp[r] = p[q];
-                s_loff[r] = off[q];
-                s_lcell[r] = lcells + linc - nt;
+                s_loff[r] = o;
+                s_lcell[r] = lo_cell;
                 s_lbox[r] = tb[q];
                 tb[q] = make_ushort4(1, 1, 0, 0);    // nothing left for the lane to write
+                lo_cell += nt[q];
+                ++lr;
             }
-            cells += __shfl_sync(0xFFFFFFFFu, inc, 31);
-            lcells += __shfl_sync(0xFFFFFFFFu, linc, 31);
-            nl += __popc(bal);
+            o += nt[q];
         }
         if (lane == 0) {
             s_wtot[0][warp] = cells;
