@@ -586,7 +586,6 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     a.ev = at<uint32_t>(ws, L.off_ev[0]);
     a.cap = L.cap;
     a.nsx = (int)L.nsx;
-    a.sshift = tshift + 3;
     a.large_tiles = large_tiles;
     k_bin_reduce<<<a.ctas, 256, 0, st>>>(a);
     k_bin_scan<<<1, 1024, 0, st>>>(a);
@@ -631,7 +630,6 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     fa.ucnt = at<uint32_t>(ws, L.off_ucnt);
     fa.toff = at<uint32_t>(ws, L.off_toff);
     fa.list = at<uint32_t>(ws, fine_list_offset(L));
-    fa.box = at<ushort4>(ws, L.off_box);
     fa.cap = L.cap;
     fa.nsuper = L.nsuper;
     fa.nsx = L.nsx;
@@ -639,7 +637,6 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     fa.nty = (uint32_t)L.nty;
     fa.ntiles = L.ntiles;
     fa.max_units = L.max_units;
-    fa.tshift = tshift;
     k_units<<<1, 1024, 0, st>>>(fa);
     k_fine_count<<<L.max_units, 256, 0, st>>>(fa);
     k_fine_unit_scan<<<L.nsuper, 64, 0, st>>>(fa);

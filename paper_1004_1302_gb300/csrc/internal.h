@@ -49,7 +49,7 @@ struct Header {
     uint32_t visible;          // V
     uint32_t n_large;
     uint64_t tile_entries;     // D (may exceed cap on overflow)
-    uint32_t tile_entries32;   // min(D, cap), the count the entry sort works on
+    uint32_t tile_entries32;   // min(D, cap): the fine entries written
     uint32_t key_min, key_max; // over visible particles
     uint32_t sorted_buf;       // ping-pong buffer holding the ordered visible list
     uint64_t super_entries;    // entries (particle, super-tile) (may exceed cap on overflow)
@@ -153,8 +153,8 @@ struct BinArgs {
     uint32_t ctas;
     uint32_t *ek, *ev;         // emitted entries (super-tile id, particle)
     uint64_t cap;
-    int nsx, sshift;           // super-tile columns; sshift = log2(super-tile side in pixels)
-    uint32_t large_tiles;      // particles touching more super-tiles than this are written by a whole warp
+    int nsx;                   // super-tile columns
+    uint32_t large_tiles;      // particles touching more super-tiles than this have their entries dealt over the CTA
 };
 
 // Expansion of super-tile lists into fine-tile lists (64 fine tiles per super-tile).
@@ -169,10 +169,8 @@ struct FineArgs {
     uint32_t *ucnt;                // [unit][64]
     uint32_t *toff;                // fine-tile offsets (ntiles + 1)
     uint32_t *list;                // fine-tile lists
-    const ushort4 *box;
     uint64_t cap;
     uint32_t nsuper, nsx, ntx, nty, ntiles, max_units;
-    int tshift;
 };
 
 struct RenderArgs {
