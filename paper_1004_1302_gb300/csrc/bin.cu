@@ -356,19 +356,50 @@ __global__ void __launch_bounds__(256) k_fine_count(FineArgs a) {
 }
 
 // Per super-tile: each fine tile's running count over the super-tile's units
-// (exclusive, in place) and its total, written as the fine tile's count.
-__global__ void __launch_bounds__(64) k_fine_unit_scan(FineArgs a) {
-    const uint32_t s = blockIdx.x, t = threadIdx.x;
-    uint32_t run = 0;
-    const uint32_t u1 = min(a.ufirst[s + 1], a.max_units);
-    for (uint32_t u = a.ufirst[s]; u < u1; ++u) {
+// (exclusive, in place) and its total, written as the fine tile's count.  The
+// units are cut into 16 chunks: each chunk's sum, a scan over the chunks per
+// fine tile, then the running counts inside each chunk.
+__global__ void __launch_bounds__(1024) k_fine_unit_scan(FineArgs a) {
+    constexpr int kChunks = 16;
+    __shared__ uint32_t part[kChunks][64];
+    const uint32_t s = blockIdx.x, t = threadIdx.x & 63u, g = threadIdx.x >> 6;
+    const uint32_t u0 = a.ufirst[s], u1 = min(a.ufirst[s + 1], a.max_units);
+    const uint32_t nu = u1 > u0 ? u1 - u0 : 0u, per = (nu + kChunks - 1) / kChunks;
+    const uint32_t b = u0 + g * per, e = min(b + per, u1);
+    uint32_t sum = 0;
+    for (uint32_t u = b; u < e; ++u) sum += a.ucnt[(size_t)u * 64 + t];
+    part[g][t] = sum;
+    __syncthreads();
+    if (g == 0) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int k = 0; k < kChunks; ++k) {
+            const uint32_t v = part[k][t];
+            part[k][t] = run;
+            run += v;
+        }
+        const uint32_t tx = (s % a.nsx) * kSuperSide + (t % kSuperSide), ty = (s / a.nsx) * kSuperSide + t / kSuperSide;
+        if (tx < a.ntx && ty < a.nty) a.toff[ty * a.ntx + tx] = run;
+    }
+    __syncthreads();
+    uint32_t run = part[g][t];
+    for (uint32_t u = b; u < e; ++u) {
         const size_t q = (size_t)u * 64 + t;
         const uint32_t c = a.ucnt[q];
         a.ucnt[q] = run;
         run += c;
     }
-    const uint32_t tx = (s % a.nsx) * kSuperSide + (t % kSuperSide), ty = (s / a.nsx) * kSuperSide + t / kSuperSide;
-    if (tx < a.ntx && ty < a.nty) a.toff[ty * a.ntx + tx] = run;
+}
+
+// Super-tile offsets from the digit totals of a single grouping pass (the
+// totals are the super-tiles' entry counts).
+__global__ void __launch_bounds__(256) k_soff_from_totals(const uint32_t *htot, uint32_t *off, uint32_t nsuper) {
+    __shared__ uint32_t ws[9];
+    const uint32_t t = threadIdx.x;
+    uint32_t tot;
+    const uint32_t pre = block_exclusive_scan<256>(t < nsuper ? htot[t] : 0u, ws, &tot);
+    if (t < nsuper) off[t] = pre;
+    if (t == 0) off[nsuper] = tot;
 }
 
 // Fine-tile counts -> offsets (exclusive scan in place), total D.
@@ -618,8 +649,11 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     }
     const int f = passes & 1;
     const int sms = sm_count_bin();
-    k_group_offsets<<<sms * 8, 256, 0, st>>>(&hdr->super32, at<uint32_t>(ws, L.off_ek[f]), at<uint32_t>(ws, L.off_soff),
-                                             L.nsuper);
+    if (passes == 1)
+        k_soff_from_totals<<<1, 256, 0, st>>>(p.htot, at<uint32_t>(ws, L.off_soff), L.nsuper);
+    else
+        k_group_offsets<<<sms * 8, 256, 0, st>>>(&hdr->super32, at<uint32_t>(ws, L.off_ek[f]),
+                                                 at<uint32_t>(ws, L.off_soff), L.nsuper);
     FineArgs fa{};
     fa.hdr = hdr;
     fa.skey = at<uint32_t>(ws, L.off_ek[f]);
@@ -639,7 +673,7 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     fa.max_units = L.max_units;
     k_units<<<1, 1024, 0, st>>>(fa);
     k_fine_count<<<L.max_units, 256, 0, st>>>(fa);
-    k_fine_unit_scan<<<L.nsuper, 64, 0, st>>>(fa);
+    k_fine_unit_scan<<<L.nsuper, 1024, 0, st>>>(fa);
     k_fine_offsets<<<1, 1024, 0, st>>>(fa);
     k_fine_emit<<<L.max_units, 256, 0, st>>>(fa);
     count_launches(6);
