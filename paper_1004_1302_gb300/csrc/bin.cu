@@ -460,9 +460,6 @@ __global__ void __launch_bounds__(256) k_fine_emit(FineArgs a) {
     __shared__ uint32_t s_run[64];                  // entries placed so far per fine tile
     __shared__ uint32_t s_lb[65];                   // start of each fine tile's run in s_buf
     __shared__ unsigned long long s_gbase[64];      // list position of each fine tile's run
-    __shared__ uint32_t s_pstart[8][32];            // per warp and lane: first (entry, tile) pair of the entry
-    __shared__ uint32_t s_pinfo[8][32];             // per warp and lane: first column, first row, width, 2^16/width + 1
-    __shared__ uint32_t s_pp[8][32];                // per warp and lane: the entry's particle
     const uint32_t u = blockIdx.x;
     const uint32_t n_units = a.hdr->n_units;
     if (u >= n_units) return;
@@ -539,30 +536,33 @@ __global__ void __launch_bounds__(256) k_fine_emit(FineArgs a) {
             s_run[t] = run;
         }
         __syncthreads();
-        // (entry, fine tile) pairs of the warp, entry by entry, dealt over the lanes
+        // (entry, fine tile) pairs of the warp, entry by entry, dealt over the lanes.  The
+        // entries with pairs are the warp's first lanes and begin at distinct pair indices,
+        // so a pair's entry is (entries begun before the round) + (entries begun in the round
+        // up to the pair) - 1, from one OR-reduction and one ballot per round.
         const uint32_t w = f.c1 - f.c0 + 1, h = f.r1 - f.r0 + 1;
         const uint32_t npair = f.c0 <= f.c1 && f.r0 <= f.r1 ? w * h : 0u;
         const uint32_t pinc = warp_inclusive_scan(npair);
         const uint32_t K = __shfl_sync(0xFFFFFFFFu, pinc, 31);
-        s_pstart[warp][lane] = pinc - npair;
-        s_pinfo[warp][lane] = (uint32_t)f.c0 | ((uint32_t)f.r0 << 3) | (w << 6) | ((w ? 65536u / w + 1u : 0u) << 10);
-        s_pp[warp][lane] = p;
-        __syncwarp();
+        const uint32_t start = pinc - npair;
+        const uint32_t info = (uint32_t)f.c0 | ((uint32_t)f.r0 << 3) | (w << 6) | ((w ? 65536u / w + 1u : 0u) << 10);
+        const uint32_t le = lanemask_lt() | (1u << lane);
         for (uint32_t q0 = 0; q0 < K; q0 += 32) {
+            const bool begins = npair && start >= q0 && start < q0 + 32;
+            const uint32_t H = __reduce_or_sync(0xFFFFFFFFu, begins ? 1u << (start - q0) : 0u);
+            const uint32_t before = __popc(__ballot_sync(0xFFFFFFFFu, npair && start < q0));
+            const uint32_t o = min(before + __popc(H & le), 32u) - 1u;   // no entry begun: lane 31 (unused)
+            const uint32_t ostart = __shfl_sync(0xFFFFFFFFu, start, o);
+            const uint32_t oinfo = __shfl_sync(0xFFFFFFFFu, info, o);
+            const uint32_t pp = __shfl_sync(0xFFFFFFFFu, p, o);
             const uint32_t q = q0 + lane;
             if (q < K) {
-                uint32_t o = 0;                  // last lane whose pairs start at or before q
-#pragma unroll
-                for (uint32_t d = 16; d > 0; d >>= 1)
-                    if (s_pstart[warp][o + d] <= q) o += d;
-                const uint32_t k = q - s_pstart[warp][o];
-                const uint32_t info = s_pinfo[warp][o];
-                const uint32_t ow = (info >> 6) & 15u;
-                const uint32_t rr = (k * (info >> 10)) >> 16, cc = k - rr * ow;
-                const uint32_t r = (info >> 3 & 7u) + rr, c = (info & 7u) + cc;
+                const uint32_t k = q - ostart;
+                const uint32_t ow = (oinfo >> 6) & 15u;
+                const uint32_t rr = (k * (oinfo >> 10)) >> 16, cc = k - rr * ow;
+                const uint32_t r = (oinfo >> 3 & 7u) + rr, c = (oinfo & 7u) + cc;
                 const uint32_t t = r * kSuperSide + c;
                 const uint32_t kk = s_pos[warp][t] + __popc(s_b[warp][r] & s_b[warp][kSuperSide + c] & ((1u << o) - 1u));
-                const uint32_t pp = s_pp[warp][o];
                 if (staged) {
                     const uint32_t qq = s_lb[t] + kk;
                     if (qq < (uint32_t)kFineBuf) s_buf[qq] = pp;
