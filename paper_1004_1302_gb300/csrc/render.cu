@@ -1,19 +1,25 @@
-// Tile renderer: one CTA per screen tile, two horizontally adjacent pixels
-// per thread.  The tile's particle list is staged in batches into shared
-// memory (prefetched into registers one batch ahead).  Each warp covers an
-// 8x8 pixel block as four groups of 8 lanes, one per 4x4 quadrant: a lane
-// tests one particle of the batch against the four quadrants, four ballots
-// give each group its own list of surviving particles, and every group walks
-// its list in list order, one particle per step, all groups in the same
-// steps (a group that is done takes a null particle that adds nothing, so the
-// steps have no branch).  Per pixel it evaluates the truncated Gaussian
-// footprint (Section 2, first item) and integrates Eq. 1 (Section 2) across
-// the particle layer:
+// Tile renderer: one CTA per screen tile.  The tile's particle list is
+// staged in batches into shared memory (prefetched into registers one batch
+// ahead).  Lanes work in groups, one group per 4x4 pixel quadrant: a lane
+// tests one particle of the batch against every quadrant of its warp, one
+// ballot per quadrant gives each group its own list of surviving particles,
+// and every group walks its list in list order, one particle per step, all
+// groups in the same steps (a group that is done takes a null particle that
+// adds nothing, so the steps have no branch).
+//   tiles of 16 and 32: a warp covers a 16x8 block as eight groups of four
+//     lanes, each lane a 2x2 pixel square (the column offsets are shared by
+//     its two rows); 128 pixels per warp step
+//   tiles of 8: a warp covers the 8x8 tile as four groups of eight lanes,
+//     each lane two horizontally adjacent pixels; 64 pixels per warp step
+// Per pixel it evaluates the truncated Gaussian footprint (Section 2, first
+// item) and integrates Eq. 1 (Section 2) across the particle layer:
 //   emission    C += E g
 //   absorptive  C += T_acc S, T_acc *= T, with T = exp(-A g),
 //               S = E (1 - T)/A (E g when A = 0)
 //   E = A       C += E g, then I = 1 - exp(-C)
-// Packed f32x2 arithmetic does both pixels of a thread in one instruction.
+// Packed f32x2 arithmetic does a pair of horizontally adjacent pixels in one
+// instruction.  Both layouts composite each pixel with the same operations in
+// the same order, so they give the same image bit for bit.
 #include "internal.h"
 #include "device_util.cuh"
 
@@ -43,7 +49,7 @@ __device__ __forceinline__ float2 q_series(float2 yn) {
 }
 
 // A staged particle is laid out as ready-made operand pairs for the packed
-// two-pixel arithmetic, in four arrays (conflict-free stores):
+// pixel-pair arithmetic, in four arrays (conflict-free stores):
 // {-sx, -sx, -sy, -sy}, {k, k, -A, -A}, {Er, Er, Eg, Eg}, {Eb, Eb, r2, A}
 // with k = -log2(e)/sigma_pix^2.
 
@@ -220,11 +226,211 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile,
     }
 }
 
+// Threads of the CTA that renders a T x T tile: 2 x 2 pixels per thread for
+// T >= 16, 2 x 1 for T = 8.
+constexpr int render_threads(int T) { return T >= 16 ? T * T / 4 : T * T / 2; }
+
+// The same tile render with four pixels per lane (T >= 16): a warp covers a
+// 16 x 8 block as eight groups of 4 lanes, one per 4 x 4 quadrant, each lane
+// a 2 x 2 square (two packed pixel pairs, one per row).  A step now composites
+// eight particles (one per group) on 128 pixels, and the column terms are
+// shared by the two rows.
+template <int T, int MODE, int B, bool SERIES>
+__device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile, RenderSmem<B> &sm) {
+    constexpr int kThreads = T * T / 4;
+    constexpr int WX = 16, WY = 8;
+    constexpr int kWarpCols = T / WX;
+    constexpr int kPer = (B + kThreads - 1) / kThreads;
+    auto &s0 = sm.s0;
+    auto &s1 = sm.s1;
+    auto &s2 = sm.s2;
+    auto &s3 = sm.s3;
+    auto &scull = sm.scull;
+
+    const int tx = tile % a.ntx, ty = tile / a.ntx;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wx0 = tx * T + (warp % kWarpCols) * WX, wy0 = ty * T + (warp / kWarpCols) * WY;
+    const int grp = lane >> 2, gl = lane & 3;
+    const int px0 = wx0 + (grp & 3) * 4 + 2 * (gl & 1), py0 = wy0 + (grp >> 2) * 4 + 2 * (gl >> 1);
+    const float2 cx = make_float2((float)px0 + 0.5f, (float)px0 + 1.5f);
+    const float2 cyA = f2((float)py0 + 0.5f), cyB = f2((float)py0 + 1.5f);
+    const float bx = (float)wx0 + 0.5f, by = (float)wy0 + 0.5f;   // first pixel centre of the warp's block
+
+    float2 crA = f2(0.f), cgA = f2(0.f), cbA = f2(0.f), tA = f2(1.f);
+    float2 crB = f2(0.f), cgB = f2(0.f), cbB = f2(0.f), tB = f2(1.f);
+
+    const bool ok = a.hdr->status == SPLOTCH_OK;
+    const uint32_t begin = ok ? a.toff[tile] : 0u, end = ok ? a.toff[tile + 1] : 0u;
+
+    float4 rg[kPer], rc[kPer];
+    auto load = [&](uint32_t base) {
+        const uint32_t nb = min((uint32_t)B, end - base);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t j = threadIdx.x + q * kThreads;
+            if (j < nb && SPL_CHECK(a.hdr, base + j < a.hdr->layout.cap)) {
+                const uint32_t p = __ldg(&a.list[base + j]);
+                if (SPL_CHECK(a.hdr, p < a.hdr->layout.n)) {
+                    rg[q] = __ldg(&a.geo[p]);
+                    rc[q] = __ldg(&a.col[p]);
+                }
+            }
+        }
+    };
+    auto store = [&](int buf, uint32_t base) {
+        const uint32_t nb = min((uint32_t)B, end - base);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t j = threadIdx.x + q * kThreads;
+            if (j < nb) {
+                const float4 g = rg[q], c = rc[q];
+                s0[buf][j] = make_float4(-g.x, -g.x, -g.y, -g.y);
+                s1[buf][j] = make_float4(g.w, g.w, -c.w, -c.w);
+                s2[buf][j] = make_float4(c.x, c.x, c.y, c.y);
+                s3[buf][j] = make_float4(c.z, c.z, g.z, c.w);
+                scull[buf][j] = g;
+            }
+        }
+    };
+
+    if (threadIdx.x < 2) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        s0[threadIdx.x][B] = z;
+        s1[threadIdx.x][B] = z;
+        s2[threadIdx.x][B] = z;
+        s3[threadIdx.x][B] = z;
+    }
+    if (begin < end) {
+        load(begin);
+        store(0, begin);
+    }
+    int buf = 0;
+    // one row (pixel pair) of the lane's square: weight, transfer and colour
+    auto row = [&](const float2 d2, const float4 p1, const float4 p2, const float4 p3, float2 &cr, float2 &cg,
+                   float2 &cb, float2 &tacc) {
+        const float2 arg = __fmul2_rn(d2, make_float2(p1.x, p1.y));
+        float2 w;
+        w.x = d2.x < p3.z ? ex2_approx(arg.x) : 0.0f;
+        w.y = d2.y < p3.z ? ex2_approx(arg.y) : 0.0f;
+        if (MODE == SPLOTCH_ABSORPTIVE) {
+            const float2 na = make_float2(p1.z, p1.w);
+            if (SERIES || p3.w <= kSeriesMaxA) {
+                const float2 q = q_series(__fmul2_rn(w, na));
+                w = __fmul2_rn(tacc, __fmul2_rn(w, q));
+                tacc = __ffma2_rn(na, w, tacc);
+            } else {
+                const float2 yl = __fmul2_rn(w, f2(-1.4426950408889634f * p3.w));
+                const float2 t = make_float2(ex2_approx(yl.x), ex2_approx(yl.y));
+                w = __fmul2_rn(__fadd2_rn(f2(1.0f), make_float2(-t.x, -t.y)), f2(1.0f / p3.w));
+                w = __fmul2_rn(tacc, w);
+                tacc = __fmul2_rn(tacc, t);
+            }
+        }
+        cr = __ffma2_rn(w, make_float2(p2.x, p2.y), cr);
+        cg = __ffma2_rn(w, make_float2(p2.z, p2.w), cg);
+        cb = __ffma2_rn(w, make_float2(p3.x, p3.y), cb);
+    };
+    auto apply = [&](const int j) {
+        const float4 p0 = s0[buf][j], p1 = s1[buf][j];
+        const float4 p2 = s2[buf][j], p3 = s3[buf][j];
+        const float2 dx = __fadd2_rn(cx, make_float2(p0.x, p0.y));
+        const float2 dx2 = __fmul2_rn(dx, dx);
+        const float2 dyA = __fadd2_rn(cyA, make_float2(p0.z, p0.w));
+        const float2 dyB = __fadd2_rn(cyB, make_float2(p0.z, p0.w));
+        row(__ffma2_rn(dyA, dyA, dx2), p1, p2, p3, crA, cgA, cbA, tA);
+        row(__ffma2_rn(dyB, dyB, dx2), p1, p2, p3, crB, cgB, cbB, tB);
+    };
+    for (uint32_t base = begin; base < end; base += B, buf ^= 1) {
+        const uint32_t next = base + B;
+        if (next < end) load(next);
+        __syncthreads();
+        const uint32_t nb = min((uint32_t)B, end - base);
+        for (uint32_t c = 0; c < nb; c += 32) {
+            // each lane tests entry c + lane against the eight quadrants (4 columns x 2 rows)
+            bool k[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) k[q] = false;
+            if (c + lane < nb) {
+                const float4 g = scull[buf][c + lane];
+                const float lim = g.z * 1.0001f + 0.01f;   // conservative: never culls a pixel the exact test keeps
+                float dc[4], dr[2];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float x0 = bx + 4.0f * q;
+                    const float d = g.x - fminf(fmaxf(g.x, x0), x0 + 3.0f);
+                    dc[q] = d * d;
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float y0 = by + 4.0f * q;
+                    const float d = g.y - fminf(fmaxf(g.y, y0), y0 + 3.0f);
+                    dr[q] = d * d;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) k[q] = dc[q & 3] + dr[q >> 2] <= lim;
+            }
+            uint32_t mask = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const uint32_t m = __ballot_sync(0xFFFFFFFFu, k[q]);
+                if (grp == q) mask = m;
+            }
+            const int n_it = (int)__reduce_max_sync(0xFFFFFFFFu, (uint32_t)__popc(mask));
+            int it = 0;
+            if (MODE != SPLOTCH_ABSORPTIVE) {
+                for (; it + 1 < n_it; it += 2) {
+                    const int j0 = mask ? (int)c + __ffs(mask) - 1 : B;
+                    mask &= mask - 1;
+                    const int j1 = mask ? (int)c + __ffs(mask) - 1 : B;
+                    mask &= mask - 1;
+                    apply(j0);
+                    apply(j1);
+                }
+            }
+            for (; it < n_it; ++it) {
+                const int j = mask ? (int)c + __ffs(mask) - 1 : B;
+                mask &= mask - 1;
+                apply(j);
+            }
+        }
+        __syncthreads();
+        if (next < end) store(buf ^ 1, next);
+    }
+
+    if (MODE == SPLOTCH_E_EQ_A) {
+        crA = make_float2(-expm1f(-crA.x), -expm1f(-crA.y));
+        cgA = make_float2(-expm1f(-cgA.x), -expm1f(-cgA.y));
+        cbA = make_float2(-expm1f(-cbA.x), -expm1f(-cbA.y));
+        crB = make_float2(-expm1f(-crB.x), -expm1f(-crB.y));
+        cgB = make_float2(-expm1f(-cgB.x), -expm1f(-cgB.y));
+        cbB = make_float2(-expm1f(-cbB.x), -expm1f(-cbB.y));
+    }
+    auto put = [&](int py, float2 cr, float2 cg, float2 cb) {
+        if (py >= a.height) return;
+        float *rowp = a.image + (size_t)py * a.width * 3;
+        if (px0 < a.width) {
+            rowp[3 * px0 + 0] = cr.x; rowp[3 * px0 + 1] = cg.x; rowp[3 * px0 + 2] = cb.x;
+        }
+        if (px0 + 1 < a.width) {
+            rowp[3 * px0 + 3] = cr.y; rowp[3 * px0 + 4] = cg.y; rowp[3 * px0 + 5] = cb.y;
+        }
+    };
+    put(py0, crA, cgA, cbA);
+    put(py0 + 1, crB, cgB, cbB);
+}
+
+// Tile render with the layout for the tile size.
+template <int T, int MODE, int B, bool SERIES>
+__device__ __forceinline__ void render_any(const RenderArgs &a, const int tile, RenderSmem<B> &sm) {
+    if constexpr (T >= 16) render_tile4<T, MODE, B, SERIES>(a, tile, sm);
+    else render_tile<T, MODE, B, SERIES>(a, tile, sm);
+}
+
 template <int T, int MODE, int B>
-__global__ void __launch_bounds__(T * T / 2) k_render(RenderArgs a) {
+__global__ void __launch_bounds__(render_threads(T)) k_render(RenderArgs a) {
     __shared__ __align__(16) RenderSmem<B> sm;
-    if (MODE == SPLOTCH_ABSORPTIVE && a.hdr->series_only) render_tile<T, MODE, B, true>(a, blockIdx.x, sm);
-    else render_tile<T, MODE, B, false>(a, blockIdx.x, sm);
+    if (MODE == SPLOTCH_ABSORPTIVE && a.hdr->series_only) render_any<T, MODE, B, true>(a, blockIdx.x, sm);
+    else render_any<T, MODE, B, false>(a, blockIdx.x, sm);
 }
 
 // Persistent render of the tiles of many frames: each CTA takes the next
@@ -232,7 +438,7 @@ __global__ void __launch_bounds__(T * T / 2) k_render(RenderArgs a) {
 // order of the table (the host puts the heaviest first), so the small ones
 // fill the tail.
 template <int T, int B>
-__global__ void __launch_bounds__(T * T / 2) k_render_batch(const __grid_constant__ BatchArgs args) {
+__global__ void __launch_bounds__(render_threads(T)) k_render_batch(const __grid_constant__ BatchArgs args) {
     __shared__ __align__(16) RenderSmem<B> sm;
     __shared__ uint32_t s_task;
     for (;;) {
@@ -248,19 +454,19 @@ __global__ void __launch_bounds__(T * T / 2) k_render_batch(const __grid_constan
         }
         const RenderArgs &a = args.item[lo].args;
         const int tile = (int)(task - args.item[lo].task_begin);
-        if (a.mode == SPLOTCH_EMISSION) render_tile<T, SPLOTCH_EMISSION, B, false>(a, tile, sm);
-        else if (a.mode == SPLOTCH_ABSORPTIVE && a.hdr->series_only) render_tile<T, SPLOTCH_ABSORPTIVE, B, true>(a, tile, sm);
-        else if (a.mode == SPLOTCH_ABSORPTIVE) render_tile<T, SPLOTCH_ABSORPTIVE, B, false>(a, tile, sm);
-        else render_tile<T, SPLOTCH_E_EQ_A, B, false>(a, tile, sm);
+        if (a.mode == SPLOTCH_EMISSION) render_any<T, SPLOTCH_EMISSION, B, false>(a, tile, sm);
+        else if (a.mode == SPLOTCH_ABSORPTIVE && a.hdr->series_only) render_any<T, SPLOTCH_ABSORPTIVE, B, true>(a, tile, sm);
+        else if (a.mode == SPLOTCH_ABSORPTIVE) render_any<T, SPLOTCH_ABSORPTIVE, B, false>(a, tile, sm);
+        else render_any<T, SPLOTCH_E_EQ_A, B, false>(a, tile, sm);
     }
 }
 
 template <int T, int MODE>
 static void launch_tb(const RenderArgs &a, int ntiles, cudaStream_t st) {
     switch (a.batch) {
-    case 64: k_render<T, MODE, 64><<<ntiles, T * T / 2, 0, st>>>(a); break;
-    case 128: k_render<T, MODE, 128><<<ntiles, T * T / 2, 0, st>>>(a); break;
-    default: k_render<T, MODE, 256><<<ntiles, T * T / 2, 0, st>>>(a); break;
+    case 64: k_render<T, MODE, 64><<<ntiles, render_threads(T), 0, st>>>(a); break;
+    case 128: k_render<T, MODE, 128><<<ntiles, render_threads(T), 0, st>>>(a); break;
+    default: k_render<T, MODE, 256><<<ntiles, render_threads(T), 0, st>>>(a); break;
     }
 }
 
@@ -307,10 +513,10 @@ static cudaError_t launch_batch_tb(const BatchArgs &b, cudaStream_t st) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_batch<T, B>, T * T / 2, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_batch<T, B>, render_threads(T), 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    k_render_batch<T, B><<<sms * per_sm, T * T / 2, 0, st>>>(b);
+    k_render_batch<T, B><<<sms * per_sm, render_threads(T), 0, st>>>(b);
     return cudaGetLastError();
 }
 
