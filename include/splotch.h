@@ -214,7 +214,11 @@ int splotch_colorize(const splotch_particles *p, const splotch_species *species,
 int splotch_render(const splotch_render_params *params, const splotch_camera *cam, uint64_t n, void *workspace,
                    size_t workspace_bytes, float *image, void *stream);
 
-/* The three parts of splotch_render, callable one by one (same arguments). */
+/* The three parts of splotch_render, callable one by one (same arguments).
+ * splotch_bin also records the order in which splotch_render_tiles starts
+ * the tiles (longest lists first); it changes when a tile is rendered, never
+ * the image.  splotch_render_tiles needs a workspace that splotch_bin has
+ * processed for this frame. */
 int splotch_sort(const splotch_render_params *params, const splotch_camera *cam, uint64_t n, void *workspace,
                  size_t workspace_bytes, void *stream);
 int splotch_bin(const splotch_render_params *params, const splotch_camera *cam, uint64_t n, void *workspace,

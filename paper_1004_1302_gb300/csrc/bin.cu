@@ -402,10 +402,27 @@ __global__ void __launch_bounds__(256) k_soff_from_totals(const uint32_t *htot, 
     if (t == 0) off[nsuper] = tot;
 }
 
-// Fine-tile counts -> offsets (exclusive scan in place), total D.
+// Render cost class of a tile from its list length c: c itself below 4,
+// else four classes per power of two (the two bits after the leading one).
+constexpr int kCostClasses = 128;
+__device__ __forceinline__ int cost_class(uint32_t c) {
+    if (c < 4) return (int)c;
+    const int e = 31 - __clz(c);
+    return min(kCostClasses - 1, e * 4 + (int)((c >> (e - 2)) & 3u));
+}
+
+// Fine-tile counts -> offsets (exclusive scan in place), total D.  Also the
+// render order of the tiles: longest lists first (by cost class), so that
+// the tiles that take longest start first and the short ones fill the end of
+// the render instead of one long tile running on alone.  The order inside a
+// class is whatever the atomics give: the tiles are independent, so the
+// order changes when a tile runs, never the image.
 __global__ void __launch_bounds__(1024) k_fine_offsets(FineArgs a) {
     __shared__ unsigned long long ws[33];
+    __shared__ uint32_t s_class[kCostClasses];
     constexpr int kPer = 8;
+    if (threadIdx.x < kCostClasses) s_class[threadIdx.x] = 0;
+    __syncthreads();
     unsigned long long carry = 0;
     for (uint32_t base = 0; base < a.ntiles; base += 1024 * kPer) {
         uint32_t v[kPer];
@@ -421,8 +438,13 @@ __global__ void __launch_bounds__(1024) k_fine_offsets(FineArgs a) {
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const uint32_t j = base + threadIdx.x * kPer + q;
-            if (j < a.ntiles) a.toff[j] = (uint32_t)(run < a.cap ? run : a.cap);
+            const unsigned long long lo = run < a.cap ? run : a.cap;
             run += v[q];
+            const unsigned long long hi = run < a.cap ? run : a.cap;
+            if (j < a.ntiles) {
+                a.toff[j] = (uint32_t)lo;
+                atomicAdd(&s_class[cost_class((uint32_t)(hi - lo))], 1u);   // the length the render will see
+            }
         }
         carry += tot;
     }
@@ -433,6 +455,18 @@ __global__ void __launch_bounds__(1024) k_fine_offsets(FineArgs a) {
         a.hdr->tile_entries = exact || carry > a.hdr->tile_entries ? carry : a.hdr->tile_entries;
         a.hdr->tile_entries32 = (uint32_t)(carry < a.cap ? carry : a.cap);
         if (carry > a.cap) a.hdr->status = SPLOTCH_ERR_WORKSPACE;
+        // first position of each class, heaviest class first
+        uint32_t at = 0;
+        for (int k = kCostClasses - 1; k >= 0; --k) {
+            const uint32_t h = s_class[k];
+            s_class[k] = at;
+            at += h;
+        }
+    }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < a.ntiles; j += 1024) {
+        const uint32_t pos = atomicAdd(&s_class[cost_class(a.toff[j + 1] - a.toff[j])], 1u);
+        if (SPL_CHECK(a.hdr, pos < a.ntiles)) a.torder[pos] = j;
     }
 }
 
@@ -663,6 +697,7 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     fa.units = at<uint4>(ws, L.off_units);
     fa.ucnt = at<uint32_t>(ws, L.off_ucnt);
     fa.toff = at<uint32_t>(ws, L.off_toff);
+    fa.torder = at<uint32_t>(ws, L.off_torder);
     fa.list = at<uint32_t>(ws, fine_list_offset(L));
     fa.cap = L.cap;
     fa.nsuper = L.nsuper;

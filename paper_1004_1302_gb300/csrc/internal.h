@@ -36,6 +36,7 @@ struct Layout {
     uint64_t off_part;
     uint64_t off_hist, off_htot;
     uint64_t off_toff;                 // fine-tile offsets (ntiles + 1)
+    uint64_t off_torder;               // render order of the tiles (ntiles): heaviest lists first
     uint64_t off_soff, off_ufirst;     // super-tile offsets (nsuper + 1), first unit of each super-tile (nsuper + 1)
     uint64_t off_units, off_ucnt;      // units (super-tile, begin, end), per-unit counts of the 64 fine tiles
     uint64_t off_ek[2], off_ev[2];     // super-tile entries (ping-pong); the final fine list reuses the free key buffer
@@ -169,6 +170,7 @@ struct FineArgs {
     uint32_t *ucnt;                // [unit][64]
     uint32_t *toff;                // fine-tile offsets (ntiles + 1)
     uint32_t *list;                // fine-tile lists
+    uint32_t *torder;              // render order of the tiles (ntiles)
     uint64_t cap;
     uint32_t nsuper, nsx, ntx, nty, ntiles, max_units;
 };
@@ -176,6 +178,7 @@ struct FineArgs {
 struct RenderArgs {
     const Header *hdr;
     const uint32_t *toff;      // ntiles + 1
+    const uint32_t *torder;    // ntiles: tiles in render order (a permutation)
     const uint32_t *list;      // tile-sorted particle indices
     const float4 *geo;         // sx, sy, r2, -log2(e)/sigma_pix^2
     const float4 *col;         // Er, Eg, Eb, A

@@ -429,14 +429,16 @@ __device__ __forceinline__ void render_any(const RenderArgs &a, const int tile, 
 template <int T, int MODE, int B>
 __global__ void __launch_bounds__(render_threads(T)) k_render(RenderArgs a) {
     __shared__ __align__(16) RenderSmem<B> sm;
-    if (MODE == SPLOTCH_ABSORPTIVE && a.hdr->series_only) render_any<T, MODE, B, true>(a, blockIdx.x, sm);
-    else render_any<T, MODE, B, false>(a, blockIdx.x, sm);
+    const uint32_t tile = __ldg(&a.torder[blockIdx.x]);
+    if (tile >= gridDim.x) return;   // a workspace that was never binned
+    if (MODE == SPLOTCH_ABSORPTIVE && a.hdr->series_only) render_any<T, MODE, B, true>(a, (int)tile, sm);
+    else render_any<T, MODE, B, false>(a, (int)tile, sm);
 }
 
 // Persistent render of the tiles of many frames: each CTA takes the next
 // (frame, tile) task from a counter until none is left.  Frames come in the
-// order of the table (the host puts the heaviest first), so the small ones
-// fill the tail.
+// order of the table (the host puts the heaviest first) and a frame's tiles
+// in its render order (longest lists first), so the small ones fill the tail.
 template <int T, int B>
 __global__ void __launch_bounds__(render_threads(T)) k_render_batch(const __grid_constant__ BatchArgs args) {
     __shared__ __align__(16) RenderSmem<B> sm;
@@ -453,7 +455,11 @@ __global__ void __launch_bounds__(render_threads(T)) k_render_batch(const __grid
             if (args.item[mid].task_begin <= task) lo = mid; else hi = mid;
         }
         const RenderArgs &a = args.item[lo].args;
-        const int tile = (int)(task - args.item[lo].task_begin);
+        const uint32_t first = args.item[lo].task_begin;
+        const uint32_t last = lo + 1 < args.n_items ? args.item[lo + 1].task_begin : args.n_tasks;
+        const uint32_t t = __ldg(&a.torder[task - first]);
+        if (t >= last - first) continue;   // a workspace that was never binned
+        const int tile = (int)t;
         if (a.mode == SPLOTCH_EMISSION) render_any<T, SPLOTCH_EMISSION, B, false>(a, tile, sm);
         else if (a.mode == SPLOTCH_ABSORPTIVE && a.hdr->series_only) render_any<T, SPLOTCH_ABSORPTIVE, B, true>(a, tile, sm);
         else if (a.mode == SPLOTCH_ABSORPTIVE) render_any<T, SPLOTCH_ABSORPTIVE, B, false>(a, tile, sm);
@@ -483,6 +489,7 @@ RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, floa
     RenderArgs a{};
     a.hdr = header(ws);
     a.toff = at<uint32_t>(ws, L.off_toff);
+    a.torder = at<uint32_t>(ws, L.off_torder);
     a.list = at<uint32_t>(ws, fine_list_offset(L));
     a.geo = at<float4>(ws, L.off_geo);
     a.col = at<float4>(ws, L.off_col);

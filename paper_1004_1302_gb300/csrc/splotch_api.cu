@@ -59,6 +59,7 @@ int compute_layout(uint64_t n, int width, int height, int tile, uint64_t cap, La
     L.off_hist = take((uint64_t)kRadix * L.hist_ctas * 4);
     L.off_htot = take((uint64_t)kRadix * 4);
     L.off_toff = take(((uint64_t)L.ntiles + 1) * 4);
+    L.off_torder = take((uint64_t)L.ntiles * 4);
     L.nsx = (uint32_t)((L.ntx + kSuperSide - 1) / kSuperSide);
     L.nsy = (uint32_t)((L.nty + kSuperSide - 1) / kSuperSide);
     L.nsuper = L.nsx * L.nsy;
