@@ -377,15 +377,14 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
             }
             const int n_it = (int)__reduce_max_sync(0xFFFFFFFFu, (uint32_t)__popc(mask));
             int it = 0;
-            if (MODE != SPLOTCH_ABSORPTIVE) {
-                for (; it + 1 < n_it; it += 2) {
-                    const int j0 = mask ? (int)c + __ffs(mask) - 1 : B;
-                    mask &= mask - 1;
-                    const int j1 = mask ? (int)c + __ffs(mask) - 1 : B;
-                    mask &= mask - 1;
-                    apply(j0);
-                    apply(j1);
-                }
+            // two steps per iteration: the second step's geometry overlaps the first's compositing
+            for (; it + 1 < n_it; it += 2) {
+                const int j0 = mask ? (int)c + __ffs(mask) - 1 : B;
+                mask &= mask - 1;
+                const int j1 = mask ? (int)c + __ffs(mask) - 1 : B;
+                mask &= mask - 1;
+                apply(j0);
+                apply(j1);
             }
             for (; it < n_it; ++it) {
                 const int j = mask ? (int)c + __ffs(mask) - 1 : B;

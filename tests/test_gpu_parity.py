@@ -153,6 +153,44 @@ def test_edge_cases():
         assert g.info.large >= 1
 
 
+@pytest.mark.parametrize("case", ["ties", "extremes"])
+def test_depth_key_rounding(case):
+    """The depth is a double rounded once to float for the key (C12).  A
+    camera at x = -2^-24 looking along +x makes Z = x + 2^-24 exactly, so
+    every float x in [1, 2) lands halfway between two floats (round to even
+    picks the neighbour with an even last bit) and x in [2, 4) a quarter of
+    the way; zero and subnormal coordinates, points behind the camera and a
+    depth beyond the float range (znear = 0, eye at x = -1e38) are included."""
+    pal = synth.colormap()
+    rng = np.random.default_rng(7)
+    if case == "ties":
+        cam = synth.CameraSpec((-2.0 ** -24, 0.0, 0.0), (10.0, 0.0, 0.0), (0.0, 1.0, 0.0), 45.0, 64, 48)
+        k = np.arange(1000)
+        x = np.concatenate([1.0 + k * 2.0 ** -23, 2.0 + k * 2.0 ** -22, rng.uniform(1.0, 100.0, 1000),
+                            [-1.0, 0.0, 2.0 ** -30]])
+        y = np.concatenate([np.zeros(2000), rng.uniform(-0.01, 0.01, 1000), [0.0, 0.0, 1e-40]])
+    else:
+        cam = synth.CameraSpec((-1e38, 0.0, 0.0), (1e39, 0.0, 0.0), (0.0, 1.0, 0.0), 45.0, 64, 48, znear=0.0)
+        x = np.array([3e38, 3.3e38, 2.4e38, -1e38, 1.0, 0.0, -3e38])
+        y = np.zeros_like(x)
+    x = x.astype(np.float32)
+    n = x.size
+    sp = [synth.Species(0, n, use_log=0, brightness=1.0, absorption=0.05)]
+    ps = _ps(x, y, np.zeros(n), np.full(n, 1e-3), rng.uniform(0.5, 1.0, n), sp)
+    for mode in (1, 0):
+        g = gpu_render(ps, cam, pal, mode)
+        o = oracle_render(ps, cam, pal, mode)
+        _compare_frame(g, o)
+    if case == "ties":
+        key = g.key[:1000]
+        assert g.info.visible >= 3000
+        # x = 1 + k 2^-23 (+ 2^-24) rounds to the even one of x and its successor
+        want = np.where(k % 2 == 0, x[:1000], np.nextafter(x[:1000], np.float32(np.inf)))
+        np.testing.assert_array_equal(key, want.view(np.uint32))
+    else:
+        assert (g.key[:2] == np.uint32(0x7F800000)).all()   # beyond the float range: +inf
+
+
 @pytest.mark.slow
 def test_two_species_10m_full_size_lists_and_sampled_pixels():
     """10M particles, 1920x1080, absorptive, the launch configuration of the
