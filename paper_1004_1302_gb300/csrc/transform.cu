@@ -54,14 +54,25 @@ struct Footprint {
 // binary64: 1 + 11 + 52 bits, bias 1023).
 
 // float -> double, exact: a normal float keeps its sign and significand
-// (shifted up by 52 - 23 bits) and moves its exponent to the wider bias.
-// Zeros, subnormals, infinities and NaNs take the hardware conversion.
+// (shifted up by 52 - 23 bits) and moves its exponent to the wider bias; a
+// subnormal m 2^-149 is normalised at its leading bit p (exponent p - 149);
+// infinities and NaNs keep the all-ones exponent.
 __device__ __forceinline__ double widen(float v) {
     const uint32_t b = __float_as_uint(v);
     const uint32_t e = (b >> 23) & 0xFFu;
-    if (e - 1u >= 254u) return (double)v;
-    const uint64_t d = ((uint64_t)(b & 0x80000000u) << 32) | ((uint64_t)(e + (1023u - 127u)) << 52) |
-                       ((uint64_t)(b & 0x7FFFFFu) << 29);
+    const uint32_t m = b & 0x7FFFFFu;
+    const uint64_t s = (uint64_t)(b & 0x80000000u) << 32;
+    uint64_t d;
+    if (e - 1u < 254u) {
+        d = s | ((uint64_t)(e + (1023u - 127u)) << 52) | ((uint64_t)m << 29);
+    } else if (e == 0xFFu) {
+        d = s | (0x7FFull << 52) | ((uint64_t)m << 29);
+    } else if (m == 0u) {
+        d = s;
+    } else {
+        const int p = 31 - __clz(m);   // leading bit of the subnormal's significand
+        d = s | ((uint64_t)(p - 149 + 1023) << 52) | (((uint64_t)m << (52 - p)) & 0xFFFFFFFFFFFFFull);
+    }
     return __longlong_as_double((long long)d);
 }
 
@@ -76,12 +87,19 @@ __device__ __forceinline__ bool beyond(double Z, double znear) {
 // (float)Z, round to nearest even, for Z > 0 (not NaN): keep the top 23 of
 // the 52 fraction bits and round on the 29 dropped bits; a carry out of the
 // fraction steps the exponent (up to +inf, whose encoding follows the largest
-// float's).  Results below the normal range take the hardware conversion.
+// float's).  Below the normal range the significand (with its leading one)
+// is shifted onto the subnormal grid of step 2^-149 and rounded the same way.
 __device__ __forceinline__ float narrow_positive(double Z) {
     const uint64_t b = (uint64_t)__double_as_longlong(Z);
     const int e = (int)(b >> 52) - 1023 + 127;
-    if (e <= 0) return __double2float_rn(Z);
     if (e >= 255) return __uint_as_float(0x7F800000u);
+    if (e <= 0) {
+        const uint64_t sig = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int sh = 30 - e;   // bits dropped to reach the subnormal grid
+        if (sh >= 64) return 0.0f;
+        const uint64_t q = sig >> sh, rem = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        return __uint_as_float((uint32_t)(q + (rem > half || (rem == half && (q & 1ull)))));
+    }
     const uint32_t hi = (uint32_t)(b >> 29) & 0x7FFFFFu;
     const uint32_t rem = (uint32_t)b & 0x1FFFFFFFu;
     uint32_t f = ((uint32_t)e << 23) | hi;
