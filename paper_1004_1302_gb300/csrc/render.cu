@@ -53,8 +53,13 @@ __device__ __forceinline__ float2 q_series(float2 yn) {
 // {-sx, -sx, -sy, -sy}, {k, k, -A, -A}, {Er, Er, Eg, Eg}, {Eb, Eb, r2, A}
 // with k = -log2(e)/sigma_pix^2.
 
+// Slots: the 2x2-pixel layout keeps each run of 32 entries after a slot of
+// its own that holds a particle adding nothing (slot 33 r for run r, entry
+// e at 33 (e / 32) + 1 + e % 32), so a step's slot is the run's base plus
+// __ffs of the group's mask, with no test for an empty mask; the two-pixel
+// layout keeps entries in order with that particle at slot B.
 template <int B> struct RenderSmem {
-    float4 s0[2][B + 1], s1[2][B + 1], s2[2][B + 1], s3[2][B + 1];   // entry B: a particle that adds nothing
+    float4 s0[2][B + B / 32 + 1], s1[2][B + B / 32 + 1], s2[2][B + B / 32 + 1], s3[2][B + B / 32 + 1];
     float4 scull[2][B];   // sx, sy, r2 for the cull test
 };
 
@@ -284,21 +289,23 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
             const uint32_t j = threadIdx.x + q * kThreads;
             if (j < nb) {
                 const float4 g = rg[q], c = rc[q];
-                s0[buf][j] = make_float4(-g.x, -g.x, -g.y, -g.y);
-                s1[buf][j] = make_float4(g.w, g.w, -c.w, -c.w);
-                s2[buf][j] = make_float4(c.x, c.x, c.y, c.y);
-                s3[buf][j] = make_float4(c.z, c.z, g.z, c.w);
+                const uint32_t sl = (j >> 5) * 33 + 1 + (j & 31);
+                s0[buf][sl] = make_float4(-g.x, -g.x, -g.y, -g.y);
+                s1[buf][sl] = make_float4(g.w, g.w, -c.w, -c.w);
+                s2[buf][sl] = make_float4(c.x, c.x, c.y, c.y);
+                s3[buf][sl] = make_float4(c.z, c.z, g.z, c.w);
                 scull[buf][j] = g;
             }
         }
     };
 
-    if (threadIdx.x < 2) {
+    if (threadIdx.x < 2 * (B / 32)) {
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        s0[threadIdx.x][B] = z;
-        s1[threadIdx.x][B] = z;
-        s2[threadIdx.x][B] = z;
-        s3[threadIdx.x][B] = z;
+        const int nbuf = threadIdx.x & 1, sl = (threadIdx.x >> 1) * 33;
+        s0[nbuf][sl] = z;
+        s1[nbuf][sl] = z;
+        s2[nbuf][sl] = z;
+        s3[nbuf][sl] = z;
     }
     if (begin < end) {
         load(begin);
@@ -378,16 +385,17 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
             const int n_it = (int)__reduce_max_sync(0xFFFFFFFFu, (uint32_t)__popc(mask));
             int it = 0;
             // two steps per iteration: the second step's geometry overlaps the first's compositing
+            const int cb = (int)(c >> 5) * 33;   // slot cb holds the null particle of this run of 32
             for (; it + 1 < n_it; it += 2) {
-                const int j0 = mask ? (int)c + __ffs(mask) - 1 : B;
+                const int j0 = cb + __ffs(mask);
                 mask &= mask - 1;
-                const int j1 = mask ? (int)c + __ffs(mask) - 1 : B;
+                const int j1 = cb + __ffs(mask);
                 mask &= mask - 1;
                 apply(j0);
                 apply(j1);
             }
             for (; it < n_it; ++it) {
-                const int j = mask ? (int)c + __ffs(mask) - 1 : B;
+                const int j = cb + __ffs(mask);
                 mask &= mask - 1;
                 apply(j);
             }
