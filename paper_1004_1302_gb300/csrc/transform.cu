@@ -3,6 +3,7 @@
 // and "display"; Section 2 for the footprint and colour.
 #include "internal.h"
 #include "device_util.cuh"
+#include "ieee754.h"
 
 namespace spl {
 
@@ -48,65 +49,6 @@ struct Footprint {
     ushort4 box;     // x0, y0, x1, y1
 };
 
-// Double-precision throughput is low on this GPU, so the exact conversions
-// around the depth's four double operations are done on the integer units,
-// from the IEEE 754 encodings (binary32: 1 + 8 + 23 bits, exponent bias 127;
-// binary64: 1 + 11 + 52 bits, bias 1023).
-
-// float -> double, exact: a normal float keeps its sign and significand
-// (shifted up by 52 - 23 bits) and moves its exponent to the wider bias; a
-// subnormal m 2^-149 is normalised at its leading bit p (exponent p - 149);
-// infinities and NaNs keep the all-ones exponent.
-__device__ __forceinline__ double widen(float v) {
-    const uint32_t b = __float_as_uint(v);
-    const uint32_t e = (b >> 23) & 0xFFu;
-    const uint32_t m = b & 0x7FFFFFu;
-    const uint64_t s = (uint64_t)(b & 0x80000000u) << 32;
-    uint64_t d;
-    if (e - 1u < 254u) {
-        d = s | ((uint64_t)(e + (1023u - 127u)) << 52) | ((uint64_t)m << 29);
-    } else if (e == 0xFFu) {
-        d = s | (0x7FFull << 52) | ((uint64_t)m << 29);
-    } else if (m == 0u) {
-        d = s;
-    } else {
-        const int p = 31 - __clz(m);   // leading bit of the subnormal's significand
-        d = s | ((uint64_t)(p - 149 + 1023) << 52) | (((uint64_t)m << (52 - p)) & 0xFFFFFFFFFFFFFull);
-    }
-    return __longlong_as_double((long long)d);
-}
-
-// Z > znear for znear >= 0: positive doubles order like their encodings read
-// as integers, negative ones (and -0) read as negative integers, and a NaN
-// (encoding above that of +inf) never passes.
-__device__ __forceinline__ bool beyond(double Z, double znear) {
-    const long long z = __double_as_longlong(Z);
-    return z > __double_as_longlong(znear) && z <= 0x7FF0000000000000ll;
-}
-
-// (float)Z, round to nearest even, for Z > 0 (not NaN): keep the top 23 of
-// the 52 fraction bits and round on the 29 dropped bits; a carry out of the
-// fraction steps the exponent (up to +inf, whose encoding follows the largest
-// float's).  Below the normal range the significand (with its leading one)
-// is shifted onto the subnormal grid of step 2^-149 and rounded the same way.
-__device__ __forceinline__ float narrow_positive(double Z) {
-    const uint64_t b = (uint64_t)__double_as_longlong(Z);
-    const int e = (int)(b >> 52) - 1023 + 127;
-    if (e >= 255) return __uint_as_float(0x7F800000u);
-    if (e <= 0) {
-        const uint64_t sig = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int sh = 30 - e;   // bits dropped to reach the subnormal grid
-        if (sh >= 64) return 0.0f;
-        const uint64_t q = sig >> sh, rem = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-        return __uint_as_float((uint32_t)(q + (rem > half || (rem == half && (q & 1ull)))));
-    }
-    const uint32_t hi = (uint32_t)(b >> 29) & 0x7FFFFFu;
-    const uint32_t rem = (uint32_t)b & 0x1FFFFFFFu;
-    uint32_t f = ((uint32_t)e << 23) | hi;
-    if (rem > 0x10000000u || (rem == 0x10000000u && (hi & 1u))) f += 1u;
-    return __uint_as_float(f);
-}
-
 // The single-precision geometry of the transform call, operation by
 // operation, each rounded on its own (no contraction).
 __device__ __forceinline__ Footprint footprint(const TransformArgs &a, float x, float y, float z, float h) {
@@ -114,10 +56,11 @@ __device__ __forceinline__ Footprint footprint(const TransformArgs &a, float x, 
     f.geo = make_float4(0.f, 0.f, 0.f, 0.f);
     f.key = kInvalidKey;
     f.box = make_ushort4(1, 1, 0, 0);
-    double Z = __dsub_rn(__fma_rn(widen(z), a.fwd2, __fma_rn(widen(y), a.fwd1, __dmul_rn(widen(x), a.fwd0))),
+    double Z = __dsub_rn(__fma_rn(ieee::widen(z), a.fwd2, __fma_rn(ieee::widen(y), a.fwd1, __dmul_rn(ieee::widen(x), a.fwd0))),
                          a.c_fwd);
-    if (!beyond(Z, a.znear)) return f;
-    float Zf = narrow_positive(Z);
+    // the depth's conversions and near-plane test on the integer units (double throughput is low)
+    if (!ieee::beyond(Z, a.znear)) return f;
+    float Zf = ieee::narrow_positive(Z);
     float X = __fsub_rn(__fmaf_rn(z, a.r2, __fmaf_rn(y, a.r1, __fmul_rn(x, a.r0))), a.cr);
     float Y = __fsub_rn(__fmaf_rn(z, a.u2, __fmaf_rn(y, a.u1, __fmul_rn(x, a.u0))), a.cu);
     float inv = __frcp_rn(Zf);
