@@ -572,17 +572,29 @@ def run_serving(args, dev):
                          "workspace_bytes": int(fr.ws_bytes), "status": int(inf.status), "stages_ms": stages}
     del fr
     torch.cuda.empty_cache()
+    # the plain renderer on the saturating requests: one slot, one request at a time
+    n_cal = min(16, args.requests)
+    serial = RenderServer(res, pal, res.species[0], tile=args.tile, batch=args.batch, max_inflight=1, device=dev)
+    one = random_requests(args.requests, res.n)[:n_cal]
+    for r in one:
+        r.arrival = 0.0
+    _, st1 = serial.serve(one)
+    del serial
+    torch.cuda.empty_cache()
     # request stream
     server = RenderServer(res, pal, res.species[0], tile=args.tile, batch=args.batch, max_inflight=8, device=dev)
     reqs = random_requests(args.requests, res.n)
-    calib = reqs[:min(16, len(reqs))]
+    calib = reqs[:n_cal]
     for r in calib:
         r.arrival = 0.0
     done, st = server.serve(calib)
     capacity = st["frames_per_s"]
     rest = poisson_arrivals(random_requests(args.requests, res.n, seed=0x5E21), 0.7 * capacity)
     done, st = server.serve(rest)
-    out["calibration"] = {"requests": len(calib), "saturated_frames_per_s": capacity}
+    out["calibration"] = {"requests": len(calib), "saturated_frames_per_s": capacity,
+                          "one_at_a_time_frames_per_s": st1["frames_per_s"],
+                          "one_at_a_time_particles_per_s": st1["particles_per_s"],
+                          "overlap_gain": capacity / st1["frames_per_s"] if st1["frames_per_s"] else None}
     out["serving"] = dict(st, arrival_rate_per_s=0.7 * capacity, budget_bytes=server.budget,
                           peak_reserved_bytes=server.peak_in_use)
     out["value"] = st["particles_per_s"]

@@ -130,3 +130,19 @@ def test_cancellation_of_waiting_and_running_requests():
     assert by[2].status == S.OK and by[4].status == S.OK
     assert by[1].admitted is None and by[3].admitted is None
     assert st["cancelled"] == 3 and st["completed"] == 2 and srv.in_use == 0
+
+
+def test_one_slot_serves_one_request_at_a_time_and_more_slots_overlap():
+    """The serving form's plain arm is the same server with one slot: its
+    requests run strictly one after another; with four slots they overlap
+    and the same work ends sooner."""
+    work = {k: 0.02 for k in range(8)}
+    clk = _Clock()
+    done1, st1 = _FakeServer(clk, work, max_inflight=1).serve(_reqs(8), clock=clk, idle_sleep=0.0)
+    spans = sorted((r.admitted, r.done) for r in done1)
+    assert st1["completed"] == 8 and all(a[1] <= b[0] for a, b in zip(spans, spans[1:]))
+    clk = _Clock()
+    done4, st4 = _FakeServer(clk, work, max_inflight=4).serve(_reqs(8), clock=clk, idle_sleep=0.0)
+    spans = sorted((r.admitted, r.done) for r in done4)
+    assert st4["completed"] == 8 and any(a[1] > b[0] for a, b in zip(spans, spans[1:]))
+    assert st4["wall_s"] < 0.5 * st1["wall_s"]
