@@ -20,7 +20,7 @@ class BatchRenderer:
     of (DeviceParticles, camera spec, palette, mode) or of dicts with those
     keys plus an optional per-frame `large_threshold_px`."""
 
-    def __init__(self, jobs, tile: int = 16, batch: int = 128, large_threshold_px: int = 0, streams: int = 4,
+    def __init__(self, jobs, tile: int = 16, batch: int = 64, large_threshold_px: int = 0, streams: int = 4,
                  groups: int = 1, device="cuda"):
         import torch
         if not 0 < len(jobs) <= S.MAX_BATCH:

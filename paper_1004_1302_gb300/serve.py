@@ -64,7 +64,7 @@ class _Slot:
 
 
 class RenderServer:
-    def __init__(self, resident, palette, species, tile: int = 16, batch: int = 128, large_threshold_px: int = 0,
+    def __init__(self, resident, palette, species, tile: int = 16, batch: int = 64, large_threshold_px: int = 0,
                  memory_budget: int | None = None, max_inflight: int = 8, keep_images: bool = False, device="cuda",
                  h_typical: float | None = None, trunc_f: float = 2.0, request_timeout_s: float | None = None):
         import torch

@@ -398,7 +398,7 @@ def make_species(sp) -> SpeciesParams:
     return s
 
 
-def make_params(mode: int, tile: int = 16, batch: int = 128, sigma_per_h: float = 1.0, trunc_f: float = 2.0,
+def make_params(mode: int, tile: int = 16, batch: int = 64, sigma_per_h: float = 1.0, trunc_f: float = 2.0,
                 large_threshold_px: int = 0, max_tile_entries: int = 0) -> RenderParams:
     p = RenderParams()
     p.mode, p.tile, p.batch = int(mode), int(tile), int(batch)
@@ -479,7 +479,7 @@ class Frame:
     structs passed to the C calls.  Grows the tile-entry capacity when a frame
     reports an overflow."""
 
-    def __init__(self, dp: DeviceParticles, cam_spec, palette, mode: int, tile: int = 16, batch: int = 128,
+    def __init__(self, dp: DeviceParticles, cam_spec, palette, mode: int, tile: int = 16, batch: int = 64,
                  sigma_per_h: float = 1.0, trunc_f: float = 2.0, large_threshold_px: int = 0,
                  max_tile_entries: int | None = None, device="cuda"):
         import torch
@@ -606,7 +606,7 @@ class HostPipeline:
     should be pinned for the copies to overlap."""
 
     def __init__(self, n: int, species, cam_spec, palette, mode: int, dtype: str = "f32", tile: int = 16,
-                 batch: int = 128, max_tile_entries: int | None = None, device="cuda"):
+                 batch: int = 64, max_tile_entries: int | None = None, device="cuda"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
