@@ -156,7 +156,7 @@ def measured_peaks():
 
 
 def run_reference(args, world, rank):
-    """The oracle (FP64 CPU renderer) on the machine's host cores, each step a
+    """The oracle (FP64 CPU renderer) on the host's cores, each step a
     bounded sample of the same workload."""
     if rank != 0:
         return
