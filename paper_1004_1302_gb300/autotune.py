@@ -7,6 +7,9 @@ the tile, batch or threshold, so the tuner only measures time.
 
 Results are cached per workload signature in a JSON file
 (``$SPLOTCH_AUTOTUNE_CACHE`` or ``~/.cache/splotch_gb300/autotune.json``).
+The signature holds the device, a hash of the loaded CUDA library, the
+frame's size, mode and intensity type, and the search space, so a cached
+choice is reused only for the kernels and the candidates it was measured on.
 """
 from __future__ import annotations
 
@@ -26,8 +29,24 @@ def cache_path() -> str:
                           os.path.join(os.path.expanduser("~"), ".cache", "splotch_gb300", "autotune.json"))
 
 
-def signature(dp, cam, mode, device_name: str) -> str:
-    return f"{device_name}|n={dp.n}|{cam.width}x{cam.height}|mode={mode}|dtype={dp.dtype}"
+_build_ids: dict = {}
+
+
+def build_id(path: str | None = None) -> str:
+    """First 12 hex digits of the SHA-256 of the CUDA library file (the loaded
+    one by default)."""
+    import hashlib
+    p = path or S.loaded_library_path() or S.LIB_PATH
+    if p not in _build_ids:
+        with open(p, "rb") as f:
+            _build_ids[p] = hashlib.sha256(f.read()).hexdigest()[:12]
+    return _build_ids[p]
+
+
+def signature(dp, cam, mode, device_name: str, space=(), lib: str | None = None) -> str:
+    lib = build_id() if lib is None else lib
+    return (f"{device_name}|lib={lib}|n={dp.n}|{cam.width}x{cam.height}|mode={mode}|dtype={dp.dtype}"
+            f"|space={list(map(list, space))}")
 
 
 def _load_cache(path):
@@ -70,7 +89,7 @@ def autotune(dp, cam, palette, mode, tiles=TILES, batches=BATCHES, threshold_fac
     import torch
     dev = torch.device(device)
     name = torch.cuda.get_device_name(dev)
-    key = signature(dp, cam, mode, name)
+    key = signature(dp, cam, mode, name, space=(tiles, batches, threshold_factors))
     path = cache_path()
     cache = _load_cache(path) if use_cache else {}
     if key in cache:

@@ -136,11 +136,17 @@ EXPORTS = ["splotch_abi_version", "splotch_status_string", "splotch_camera_init"
            "splotch_loader_create", "splotch_loader_start", "splotch_loader_wait", "splotch_loader_destroy"]
 
 _lib = None
+_lib_path = None
+
+
+def loaded_library_path() -> str | None:
+    """Path of the library that load() made the default (None before)."""
+    return _lib_path
 
 
 def load(path: str | None = None):
     """Load the CUDA library (raises if it is missing: there is no fallback)."""
-    global _lib
+    global _lib, _lib_path
     if _lib is not None and path is None:
         return _lib
     p = path or (LIB_PATH_CHECKED if os.environ.get("SPLOTCH_CHECKED") == "1" else LIB_PATH)
@@ -183,7 +189,7 @@ def load(path: str | None = None):
         f.argtypes = args
         f.restype = res
     if path is None:
-        _lib = lib
+        _lib, _lib_path = lib, p
     return lib
 
 

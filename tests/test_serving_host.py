@@ -146,3 +146,20 @@ def test_one_slot_serves_one_request_at_a_time_and_more_slots_overlap():
     spans = sorted((r.admitted, r.done) for r in done4)
     assert st4["completed"] == 8 and any(a[1] > b[0] for a, b in zip(spans, spans[1:]))
     assert st4["wall_s"] < 0.5 * st1["wall_s"]
+
+
+def test_autotune_signature_separates_builds_and_search_spaces():
+    from paper_1004_1302_gb300 import autotune as AT
+
+    class _DP:
+        n, dtype = 1000, "f32"
+
+    class _Cam:
+        width, height = 64, 32
+
+    space = ((8, 16), (64, 128), (1.0,))
+    a = AT.signature(_DP(), _Cam(), 1, "GPU", space=space, lib="aaaa")
+    assert a == AT.signature(_DP(), _Cam(), 1, "GPU", space=space, lib="aaaa")
+    assert a != AT.signature(_DP(), _Cam(), 1, "GPU", space=space, lib="bbbb")      # another build
+    assert a != AT.signature(_DP(), _Cam(), 1, "GPU", space=((16,), (64,), (1.0,)), lib="aaaa")
+    assert a != AT.signature(_DP(), _Cam(), 0, "GPU", space=space, lib="aaaa")
