@@ -107,3 +107,37 @@ def test_calls_reject_bad_workspace_before_launch(S):
 def test_product_path_has_no_fallback(S, tmp_path):
     with pytest.raises(RuntimeError):
         S.load(str(tmp_path / "missing.so"))
+
+
+def test_ctypes_structs_match_the_c_header(S, tmp_path):
+    """Every field of the binding's ctypes structures sits at the offset and
+    has the size the C compiler gives it in include/splotch.h, and each
+    structure has the same total size (a field missing on either side or a
+    changed type fails)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [(S.Particles, "splotch_particles"), (S.Camera, "splotch_camera"), (S.Colormap, "splotch_colormap"),
+             (S.SpeciesParams, "splotch_species"), (S.RenderParams, "splotch_render_params"),
+             (S.BatchItem, "splotch_batch_item"), (S.BlockFile, "splotch_block_file"),
+             (S.FrameInfo, "splotch_frame_info_t")]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "splotch.h"', "int main(void) {"]
+    for cls, cname in pairs:
+        lines.append(f'  printf("{cname} sizeof %zu 0\\n", sizeof({cname}));')
+        for name, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {name} %zu %zu\\n", offsetof({cname}, {name}), '
+                         f'sizeof((({cname} *)0)->{name}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "layout")
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {(a, b): (int(c), int(d)) for a, b, c, d in (ln.split() for ln in out if ln)}
+    for cls, cname in pairs:
+        assert got[(cname, "sizeof")][0] == ctypes.sizeof(cls), cname
+        for name, _ in cls._fields_:
+            field = getattr(cls, name)
+            assert got[(cname, name)] == (field.offset, field.size), (cname, name)
