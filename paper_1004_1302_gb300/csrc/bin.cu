@@ -448,6 +448,7 @@ __global__ void __launch_bounds__(1024) k_fine_offsets(FineArgs a) {
         }
         carry += tot;
     }
+    __syncthreads();   // every tile's class is counted before the class offsets are taken
     if (threadIdx.x == 0) {
         a.toff[a.ntiles] = (uint32_t)(carry < a.cap ? carry : a.cap);
         // after an overflow of the super-tile entries the count is only a lower bound
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(1024) k_fine_offsets(FineArgs a) {
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < a.ntiles; j += 1024) {
         const uint32_t pos = atomicAdd(&s_class[cost_class(a.toff[j + 1] - a.toff[j])], 1u);
-        if (SPL_CHECK(a.hdr, pos < a.ntiles)) a.torder[pos] = j;
+        if (SPL_CHECK(a.hdr, pos < a.ntiles) && pos < a.ntiles) a.torder[pos] = j;
     }
 }
 
