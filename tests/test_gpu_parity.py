@@ -210,3 +210,25 @@ def test_two_species_10m_full_size_lists_and_sampled_pixels():
     err = np.abs(got - o.image).max(axis=0) / np.abs(o.image).max(axis=0)
     assert (err <= TOL).all(), err
     assert g.info.large > 0
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_input_permutation_leaves_order_free_images(mode):
+    """Emission and E = A are order-independent (Section 2): permuting the
+    particles inside each species changes only the order of the FP32 sums,
+    so the image stays within the parity bound of the unpermuted one, and
+    every tile lists the same particles."""
+    ps, cam = small_two_species(30_000, 320, 180)
+    pal = synth.colormap()
+    rng = np.random.default_rng(11)
+    perm = np.concatenate([s.begin + rng.permutation(s.end - s.begin) for s in ps.species])
+    ps2 = synth.ParticleSet(ps.x[perm], ps.y[perm], ps.z[perm], ps.h[perm], ps.v[perm], ps.species)
+    g1 = gpu_render(ps, cam, pal, mode)
+    g2 = gpu_render(ps2, cam, pal, mode)
+    err = image_error(g2.image, g1.image.astype(np.float64))
+    assert (err <= TOL).all(), f"image change per channel {err}"
+    np.testing.assert_array_equal(g1.offsets, g2.offsets)
+    tiles = np.repeat(np.arange(g1.offsets.size - 1), np.diff(g1.offsets.astype(np.int64)))
+    a = np.lexsort((g1.tile_list, tiles))
+    b = np.lexsort((perm[g2.tile_list], tiles))
+    np.testing.assert_array_equal(g1.tile_list[a], perm[g2.tile_list][b])
