@@ -79,29 +79,38 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples taken while the timed region runs."""
+    """nvidia-smi clock and throttle-reason samples (every 50 ms) around the
+    timed region; the summary keeps the samples stamped inside the region
+    marked by begin() and end(), or all of them if none falls inside."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                          "-i", str(self.index), "-lms", "50"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
         time.sleep(0.3)
         return self
 
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
     def __exit__(self, *exc):
         time.sleep(0.2)
-        self.lines = []
         if self.proc:
             self.proc.terminate()
             try:
@@ -111,25 +120,35 @@ class ClockSampler:
                 out, _ = self.proc.communicate()
             self.lines = [ln for ln in out.splitlines() if ln.strip()]
 
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def summary(self):
-        sm, mx, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                sm, mx = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+            rows.append((self._stamp(f[0]), sm, mx, {nm for nm, v in zip(names, f[6:10]) if v.lower() == "active"}))
+        inside = [r for r in rows if r[0] is not None and self.t0 is not None and self.t1 is not None
+                  and self.t0 <= r[0] <= self.t1]
+        use = inside or rows
+        if not use:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+        sm = sorted(r[1] for r in use)
+        reasons = set().union(*(r[3] for r in use))
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[2] for r in use), "reasons": sorted(reasons),
+                "samples": len(use), "in_timed_region": bool(inside)}
 
 
 def render_profile_traffic():
@@ -671,6 +690,7 @@ def main():
     with ClockSampler(dev.index if dev.index is not None else 0) as clocks:
         barrier()
         torch.cuda.synchronize(dev)
+        clocks.begin()
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         start.record(stream)
         for k in range(K):
@@ -687,6 +707,7 @@ def main():
             e[4].record(stream)
         end.record(stream)
         torch.cuda.synchronize(dev)
+        clocks.end()
         barrier()
     launches = S.splotch_launch_count() - launches0
     total_ms = start.elapsed_time(end)
