@@ -492,3 +492,31 @@ def test_empty_and_all_culled(oracle_mod):
     ps = _ps([0.5, 5.0], [0.5, 0.5], [-3.0, 0.5], [0.01, 0.01], [1, 1], [Species(0, 2)])
     fr = O.render_frame(ps, cam, synth.colormap(), 1)
     assert fr.order.size == 0 and fr.image.max() == 0 and fr.tile_list.size == 0
+
+
+@pytest.mark.parametrize("tile", [4, 8, 16])
+def test_selected_pixels_equal_whole_image_and_brute_force(oracle_mod, tile):
+    """The selected-pixel renderer (the checker of the full-size GPU cases)
+    against the whole-image renderer, the untiled brute force and, without
+    truncation, the independent numpy renderer: a swapped (i, j), a wrong
+    tile index or a wrong output slot fails here.  The image is not square
+    and its sides are not multiples of the tile, so ragged tiles are hit."""
+    O = oracle_mod
+    W, H = 47, 31
+    ps, cam = _random_scene(250, 21 + tile, W, H)
+    pal = synth.colormap()
+    rng = np.random.default_rng(100 + tile)
+    pix = np.stack([rng.integers(0, W, 400), rng.integers(0, H, 400)], axis=1).astype(np.int32)
+    pix = np.concatenate([pix, [[0, 0], [W - 1, 0], [0, H - 1], [W - 1, H - 1]], pix[:5]]).astype(np.int32)
+    for mode in (0, 1, 2):
+        whole = O.render_frame(ps, cam, pal, mode, tile=tile)
+        sel = O.render_frame(ps, cam, pal, mode, tile=tile, pixels=pix).image
+        np.testing.assert_array_equal(sel, whole.image[pix[:, 1], pix[:, 0]])
+        brute = O.render_brute(whole.geo, whole.E, whole.A, whole.order, W, H, mode)
+        np.testing.assert_array_equal(sel, brute[pix[:, 1], pix[:, 0]])
+        assert sel.max() > 0.05
+    for mode in (0, 1):
+        fr = O.render_frame(ps, cam, pal, mode, tile=tile, trunc_f=40.0)
+        sel = O.render_frame(ps, cam, pal, mode, tile=tile, trunc_f=40.0, pixels=pix).image
+        ref = _numpy_brute(fr.geo, fr.E, fr.A, fr.order, W, H, mode)
+        np.testing.assert_allclose(sel, ref[pix[:, 1], pix[:, 0]], rtol=1e-12, atol=1e-14)
