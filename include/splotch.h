@@ -322,18 +322,22 @@ uint64_t splotch_launch_count(void);
  * deployment convenience of this library.
  *
  * key: device, n depth keys as splotch_transform writes them (0xFFFFFFFF for
- * a culled particle).  order: device, room for n uint32; receives the
- * indices of the non-culled keys in ascending key order, ties by ascending
- * index (the order splotch_sort gives).  count: device, one uint32, receives
- * how many indices were written.  The caller owns all three buffers.
+ * a culled particle), 16-byte aligned (the keys are read four at a time).
+ * order: device, room for n uint32; receives the indices of the non-culled
+ * keys in ascending key order, ties by ascending index (the order
+ * splotch_sort gives).  count: device, one uint32, receives how many indices
+ * were written (0xFFFFFFFF, and no order, if a library built with device
+ * index checks found a failed check).  The caller owns all three buffers.
  *
  * The sort's scratch is a fixed array inside the library (about 4.3 MB on
  * every GPU that loads it, held until the process exits); no call allocates
- * or frees memory.  n above SPLOTCH_NO_ALLOC_MAX_KEYS returns SPLOTCH_ERR_ARG
- * without enqueuing anything.  The first call on a device looks up the
- * array's device address (with that device current); make that first call
- * before capturing a stream.  All calls share the one array and it keeps the
- * last call's contents, so calls whose work overlaps on the GPU (different
+ * or frees memory.  n above SPLOTCH_NO_ALLOC_MAX_KEYS, a key pointer that is
+ * not 16-byte aligned or an order/count pointer that is not 4-byte aligned
+ * returns SPLOTCH_ERR_ARG without enqueuing anything.  Every call looks up
+ * the array's device address on the current device; the first call on a
+ * device can load the library's device code there, so make it before
+ * capturing a stream.  All calls share the one array and it keeps the last
+ * call's contents, so calls whose work overlaps on the GPU (different
  * streams, or different host threads on one device) race and must be
  * serialised by the caller.  Asynchronous on `stream` like the other calls.
  */

@@ -228,15 +228,21 @@ class Frame:
 
 
 def render_frame(ps, cam, palette, mode: int, tile: int = 16, sigma_per_h: float = 1.0, trunc_f: float = 2.0,
-                 back_to_front: bool = False, pixels: np.ndarray | None = None, image: bool = True) -> Frame:
+                 back_to_front: bool = False, pixels: np.ndarray | None = None, image: bool = True,
+                 timings: dict | None = None) -> Frame:
     """Whole frame: geometry, colour, order, tile lists and the image
-    (H x W x 3 float64), or the composite of selected pixels ((i, j) pairs)."""
+    (H x W x 3 float64), or the composite of selected pixels ((i, j) pairs).
+    `timings`, if given, receives the wall time (s) of the per-particle
+    stages ("particles") and of the compositing ("composite")."""
+    import time
     lib = _load()
+    t0 = time.perf_counter()
     geo = geometry(cam, ps.x, ps.y, ps.z, ps.h, sigma_per_h, trunc_f)
     E, A, ranges = colour(ps.v, ps.species, palette, getattr(ps, "vec", None), getattr(ps, "q", None))
     ordr = order(geo, by_depth=(mode == ABSORPTIVE))
     offsets, lst = tile_lists(cam.width, cam.height, tile, ordr, geo.bbox)
     img = None
+    t1 = time.perf_counter()
     args = (_p(offsets), _p(lst) if lst.size else _p(np.zeros(1, np.uint32)),
             _p(geo.sx), _p(geo.sy), _p(geo.sigma_pix), _p(geo.r2), _p(E), _p(A))
     if pixels is not None:
@@ -246,6 +252,9 @@ def render_frame(ps, cam, palette, mode: int, tile: int = 16, sigma_per_h: float
     elif image:
         img = np.zeros((cam.height, cam.width, 3), np.float64)
         lib.oracle_render(cam.width, cam.height, tile, mode, int(back_to_front), *args, _p(img))
+    if timings is not None:
+        timings["particles"] = t1 - t0
+        timings["composite"] = time.perf_counter() - t1
     return Frame(geo, E, A, ranges, ordr, offsets, lst, img)
 
 

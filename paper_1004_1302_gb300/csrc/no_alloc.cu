@@ -8,8 +8,6 @@
 // the sort's scratch.  This entry point therefore keeps its scratch in one
 // file-scope device array of fixed size, which every GPU that loads the
 // library holds until the process exits.
-#include <mutex>
-
 #include "internal.h"
 #include "device_util.cuh"
 
@@ -69,29 +67,29 @@ __global__ void __launch_bounds__(256) k_na_stats(const uint32_t *key, uint32_t 
     }
 }
 
+// Copies the sorted indices out.  A failed device index check (libraries
+// built with device checks only) writes no order and sets *count to
+// 0xFFFFFFFF, so the caller sees it.
 __global__ void __launch_bounds__(256) k_na_copy_out(const Header *hdr, const uint32_t *vals0, const uint32_t *vals1,
                                                      uint32_t *order, uint32_t *count) {
+    if (hdr->status != SPLOTCH_OK) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *count = 0xFFFFFFFFu;
+        return;
+    }
     const uint32_t v = hdr->visible;
     const uint32_t *src = hdr->sorted_buf ? vals1 : vals0;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < v; k += gridDim.x * blockDim.x) order[k] = src[k];
     if (blockIdx.x == 0 && threadIdx.x == 0) *count = v;
 }
 
-static std::mutex g_na_mutex;
-static unsigned char *g_na_ptr[64];
-
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current).
+// Device address of the scratch array on the current device.  In host code
+// the array's name stands for a host-side shadow, so the address the kernels
+// get is asked for on every call (a host-side query, cheap next to the
+// launches); a cached address could outlive a device reset.
 static int na_scratch(unsigned char **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SPLOTCH_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_no_alloc_scratch) != cudaSuccess || !p) return SPLOTCH_ERR_CUDA;
-        g_na_ptr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_na_ptr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_no_alloc_scratch) != cudaSuccess || !p) return SPLOTCH_ERR_CUDA;
+    *out = static_cast<unsigned char *>(p);
     return SPLOTCH_OK;
 }
 
@@ -103,6 +101,9 @@ extern "C" int splotch_sort_keys_no_alloc(const uint32_t *key, uint32_t n, uint3
                                           void *stream) {
     if (n > kNaMax) return SPLOTCH_ERR_ARG;
     if ((n && (!key || !order)) || !count) return SPLOTCH_ERR_ARG;
+    // the first pass reads the keys four at a time (16-byte vector loads)
+    if (reinterpret_cast<uintptr_t>(key) & 15u) return SPLOTCH_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(order) | reinterpret_cast<uintptr_t>(count)) & 3u) return SPLOTCH_ERR_ARG;
     unsigned char *base = nullptr;
     int s = na_scratch(&base);
     if (s) return s;

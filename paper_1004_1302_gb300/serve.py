@@ -300,42 +300,3 @@ class RenderServer:
                 "p50_ms": pct(0.50) * 1e3 if lat else None, "p99_ms": pct(0.99) * 1e3 if lat else None,
                 "mean_ms": 1e3 * sum(lat) / len(lat) if lat else None,
                 "retries": sum(r.retries for r in finished)}
-
-
-def random_requests(count: int, n_total: int, seed: int = 0x10041302, n_range=(1e6, 3e8),
-                    resolutions=((512, 512), (1024, 1024), (1920, 1080), (2560, 1440), (3840, 2160)),
-                    modes=(S.EMISSION, S.ABSORPTIVE)):
-    """Requests of the serving workload: region with a log-uniform particle
-    count (side from the set's mean density in the unit cube), random
-    resolution from the list, a camera on a random direction at 2-4 region
-    sizes from the region's centre, field of view U[30, 60] degrees."""
-    import numpy as np
-
-    from synth import CameraSpec
-    rng = np.random.default_rng(seed)
-    out = []
-    for k in range(count):
-        n = math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))
-        side = min(1.0, (n / n_total) ** (1.0 / 3.0))
-        c = rng.uniform(side / 2, 1 - side / 2, 3)
-        d = rng.normal(size=3)
-        d /= np.linalg.norm(d)
-        dist = rng.uniform(2.0, 4.0) * side
-        eye = c + dist * d
-        up = (0.0, 1.0, 0.0) if abs(d[1]) < 0.9 else (1.0, 0.0, 0.0)
-        w, h = resolutions[rng.integers(len(resolutions))]
-        cam = CameraSpec(tuple(eye), tuple(c), up, float(rng.uniform(30, 60)), int(w), int(h))
-        box = tuple(np.concatenate([c - side / 2, c + side / 2]))
-        out.append(Request(k, box, cam, int(modes[rng.integers(len(modes))])))
-    return out
-
-
-def poisson_arrivals(requests, rate: float, seed: int = 0x10041302):
-    """Arrival times of a Poisson stream with the given rate (requests/s)."""
-    import numpy as np
-    rng = np.random.default_rng(seed + 1)
-    t = 0.0
-    for r in requests:
-        t += rng.exponential(1.0 / rate)
-        r.arrival = t
-    return requests

@@ -308,3 +308,39 @@ def write_block_file(path: str, arrays, big_endian: bool = False, offset_bytes: 
         f.write(b"\0" * offset_bytes)
         for a in arrays:
             np.ascontiguousarray(a, dtype=np.float32).astype(dt).tofile(f)
+
+
+def request_stream(count: int, n_total: int, seed: int = SEED, n_range=(1e6, 3e8),
+                   resolutions=((512, 512), (1024, 1024), (1920, 1080), (2560, 1440), (3840, 2160)),
+                   modes=(0, 1)) -> list[tuple]:
+    """Requests of the serving workload as (box, camera, mode) triples: a
+    region with a log-uniform particle count (side from the set's mean
+    density in the unit cube), a random resolution from the list, a camera
+    on a random direction at 2-4 region sizes from the region's centre, field
+    of view U[30, 60] degrees, and a mode drawn from `modes`."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))
+        side = min(1.0, (n / n_total) ** (1.0 / 3.0))
+        c = rng.uniform(side / 2, 1 - side / 2, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        dist = rng.uniform(2.0, 4.0) * side
+        eye = c + dist * d
+        up = (0.0, 1.0, 0.0) if abs(d[1]) < 0.9 else (1.0, 0.0, 0.0)
+        w, h = resolutions[rng.integers(len(resolutions))]
+        cam = CameraSpec(tuple(eye), tuple(c), up, float(rng.uniform(30, 60)), int(w), int(h))
+        box = tuple(np.concatenate([c - side / 2, c + side / 2]))
+        out.append((box, cam, int(modes[rng.integers(len(modes))])))
+    return out
+
+
+def poisson_times(count: int, rate: float, seed: int = SEED) -> list[float]:
+    """Arrival times (s) of a Poisson stream with the given rate (per s)."""
+    rng = np.random.default_rng(seed + 1)
+    t, out = 0.0, []
+    for _ in range(count):
+        t += rng.exponential(1.0 / rate)
+        out.append(t)
+    return out

@@ -25,9 +25,10 @@ def resident():
 
 
 def _requests(n, count=8, seed=3):
-    from paper_1004_1302_gb300.serve import random_requests
-    return random_requests(count, n, seed=seed, n_range=(2e4, 3e5),
-                           resolutions=((128, 128), (200, 150), (256, 160)))
+    from paper_1004_1302_gb300.serve import Request
+    stream = synth.request_stream(count, n, seed=seed, n_range=(2e4, 3e5),
+                                  resolutions=((128, 128), (200, 150), (256, 160)))
+    return [Request(k, box, cam, mode) for k, (box, cam, mode) in enumerate(stream)]
 
 
 def _server(dp, **kw):

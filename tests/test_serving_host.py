@@ -33,12 +33,20 @@ def test_stats_percentiles_and_refusals():
 
 
 def test_poisson_arrivals_are_increasing_and_seeded():
-    reqs = [serve.Request(k, (0, 0, 0, 1, 1, 1), None, 0) for k in range(50)]
-    a = [r.arrival for r in serve.poisson_arrivals(reqs, rate=10.0, seed=3)]
-    reqs2 = [serve.Request(k, (0, 0, 0, 1, 1, 1), None, 0) for k in range(50)]
-    b = [r.arrival for r in serve.poisson_arrivals(reqs2, rate=10.0, seed=3)]
+    a = synth.poisson_times(50, rate=10.0, seed=3)
+    b = synth.poisson_times(50, rate=10.0, seed=3)
     assert a == b and all(x < y for x, y in zip(a, a[1:]))
     assert 2.0 < a[-1] < 10.0     # 50 arrivals at 10/s
+
+
+def test_request_stream_is_seeded_and_inside_the_unit_cube():
+    a = synth.request_stream(40, 10**9, seed=5)
+    b = synth.request_stream(40, 10**9, seed=5)
+    assert [(r[0], r[2]) for r in a] == [(r[0], r[2]) for r in b]
+    for box, cam, mode in a:
+        assert all(0.0 <= v <= 1.0 for v in box) and mode in (0, 1)
+        assert all(lo < hi for lo, hi in zip(box[:3], box[3:]))
+        assert 30.0 <= cam.fov_x_deg <= 60.0
 
 
 # --- watchdog and cancellation, with the device replaced by fakes -------------

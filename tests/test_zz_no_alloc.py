@@ -45,3 +45,7 @@ def test_no_alloc_sort_matches_allocating_sort():
     big = S.NO_ALLOC_MAX_KEYS + 1
     assert lib.splotch_sort_keys_no_alloc(ctypes.c_void_p(key.data_ptr()), big, ctypes.c_void_p(order.data_ptr()),
                                           ctypes.c_void_p(count.data_ptr()), None) == S.ERR_ARG
+    # so is a key pointer off the 16-byte boundary the vector loads need (checked on the host: no launch)
+    assert lib.splotch_sort_keys_no_alloc(ctypes.c_void_p(key.data_ptr() + 4), 16, ctypes.c_void_p(order.data_ptr()),
+                                          ctypes.c_void_p(count.data_ptr()), None) == S.ERR_ARG
+    torch.cuda.synchronize()
