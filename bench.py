@@ -40,7 +40,9 @@ def parse():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--quick", action="store_true", help="skip the emission, e2e and CPU legs")
+    ap.add_argument("--quick", action="store_true", help="skip the emission, e2e, CPU and form legs")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the precision, batching and 1.07e9-particle figures of the default run")
     ap.add_argument("--requests", type=int, default=200, help="serving form: number of requests")
     ap.add_argument("--lattice", type=int, default=1024, help="serving form: side of the resident lattice")
     ap.add_argument("--frames-only", type=int, default=0,
@@ -175,19 +177,21 @@ def measured_peaks():
 
 
 def reference_pixels(width, height, tile=16, every=8):
-    """Pixels of every `every`-th row of tiles (rows 0, every, 2 every, ...),
-    as (i, j) pairs: an evenly spread sample of the image."""
+    """Pixels of one tile in `every`, on diagonals (tile (tx, ty) with
+    (tx + 3 ty) mod every == 0), as (i, j) pairs: a sample spread evenly over
+    every row and column of tiles."""
     import numpy as np
-    rows = [j for j in range(height) if (j // tile) % every == 0]
-    jj, ii = np.meshgrid(np.asarray(rows, np.int32), np.arange(width, dtype=np.int32), indexing="ij")
-    return np.stack([ii.ravel(), jj.ravel()], axis=1).astype(np.int32)
+    jj, ii = np.meshgrid(np.arange(height, dtype=np.int32), np.arange(width, dtype=np.int32), indexing="ij")
+    keep = ((ii // tile) + 3 * (jj // tile)) % every == 0
+    return np.stack([ii[keep], jj[keep]], axis=1).astype(np.int32)
 
 
 def run_reference(args, world, rank):
     """The oracle (FP64 CPU renderer) on the host's cores, on the bench
     workload itself: every step runs all per-particle stages (geometry,
     colour, depth order, tile lists) over the whole 10M-particle set and
-    composites every 8th row of tiles of the 1920x1080 image.  A step's frame
+    composites one tile in eight of the 1920x1080 image (on diagonals, so
+    every row and column of tiles is sampled).  A step's frame
     time is the per-particle time plus the sampled compositing time scaled to
     the whole image; `value` is the particle count over that frame time."""
     if rank != 0:
@@ -216,7 +220,7 @@ def run_reference(args, world, rank):
     frame_s = float(np.mean(frames))
     value = ps.n / frame_s
     cores = O.num_threads()
-    sample = (f"all {ps.n} particles through every per-particle stage; compositing of every 8th row of 16-px tiles "
+    sample = (f"all {ps.n} particles through every per-particle stage; compositing of one 16-px tile in 8 (on diagonals) "
               f"({pix.shape[0]} of {cam.width * cam.height} pixels), scaled by {scale:.2f} to the whole frame; "
               f"frame time {frame_s:.1f} s")
     print(json.dumps({
@@ -655,6 +659,183 @@ def run_serving(args, dev):
     return out
 
 
+def rel_change(a, b):
+    """Largest per-channel |a - b| over the channel maximum of b."""
+    import numpy as np
+    a = a.detach().float().cpu().numpy().astype(np.float64).reshape(-1, 3)
+    b = b.detach().float().cpu().numpy().astype(np.float64).reshape(-1, 3)
+    top = np.abs(b).max(0)
+    return float((np.abs(a - b).max(0) / np.where(top > 0, top, 1.0)).max())
+
+
+def figure_early_termination(args, dev, stream, dp, cam, pal, ref_img, cutoff=1e-6):
+    """The bench frame with absorptive early termination at `cutoff` (off by
+    default in the library): frame and render time, and the largest change
+    of the image against the full integral (bounded by the cutoff times each
+    channel's maximum)."""
+    from paper_1004_1302_gb300 import splotch as S
+    fe = S.Frame(dp, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev, t_min_cutoff=cutoff)
+    img = fe.render().clone()
+    med, mean = time_frames(fe, args.steps, 3, stream)
+    st = stage_times(fe, args.steps, 3, stream)
+    return {"t_min_cutoff": cutoff, "ms_per_step": mean, "p50_ms": med, "value": dp.n / (mean * 1e-3),
+            "unit": "particles/s", "render_ms": st["render"],
+            "max_change_over_channel_max": rel_change(img, ref_img), "bound": cutoff,
+            "status": int(fe.info().status)}
+
+
+def figure_depth_slabs(args, dev, stream, dp, cam, pal, ref_img, keys, n_slabs=2):
+    """The bench frame rendered as depth slabs of equal particle count, each
+    a partial image (C, T), composed nearest first on the device: the one GPU
+    building block of a depth-sharded render (every slab would be a GPU)."""
+    import numpy as np
+    import torch
+
+    from paper_1004_1302_gb300 import splotch as S
+    from paper_1004_1302_gb300.compose import compose_device
+    vis = np.sort(keys[keys != 0xFFFFFFFF].astype(np.int64))
+    bounds = [0] + [int(vis[(k * vis.size) // n_slabs]) for k in range(1, n_slabs)] + [0xFFFFFFFF]
+    frames = [S.Frame(dp, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev,
+                      slab=(bounds[k], bounds[k + 1])) for k in range(n_slabs)]
+    for f in frames:
+        f.render_partial()
+    acc = (torch.empty_like(ref_img), torch.empty_like(ref_img))
+
+    def run():
+        for f in frames:
+            f.run_partial()
+        compose_device((frames[0].image, frames[0].trans), (frames[1].image, frames[1].trans), out=acc)
+        for f in frames[2:]:
+            compose_device(acc, (f.image, f.trans), out=acc)
+
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        run()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / args.steps
+    status = [int(f.info().status) for f in frames]
+    return {"slabs": n_slabs, "ms_per_step": ms, "value": dp.n / (ms * 1e-3), "unit": "particles/s",
+            "max_change_over_channel_max": rel_change(acc[0], ref_img), "status": status,
+            "exchange_bytes_per_slab": int(2 * ref_img.numel() * 4),
+            "what": "every slab rendered on this GPU one after the other, then composed on the device"}
+
+
+def figure_precision(args, dev, stream):
+    """Clustered set, 100M particles, intensity stored FP32 and FP16
+    (positions and h FP32, FP32 accumulation), absorptive 1920x1080."""
+    import torch
+
+    import synth
+    from paper_1004_1302_gb300 import splotch as S
+    ps, cam = synth.clustered()
+    pal = synth.colormap()
+    out, imgs = {"particles": ps.n, "workload": "clustered set: 100M particles, 5000 Plummer spheres + 10% uniform, "
+                                                "1920x1080, absorptive"}, {}
+    for dtype in ("f32", "f16"):
+        dp = S.upload(ps, dev, dtype)
+        fr = S.Frame(dp, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev)
+        imgs[dtype] = fr.render().clone()
+        med, mean = time_frames(fr, 5, 3, stream)
+        out[dtype] = {"ms_per_step": mean, "value": ps.n / (mean * 1e-3), "input_bytes_per_particle":
+                      16 + (4 if dtype == "f32" else 2), "status": int(fr.info().status)}
+        del fr, dp
+        torch.cuda.empty_cache()
+    out["f16_change_over_channel_max"] = rel_change(imgs["f16"], imgs["f32"])
+    out["parity"] = ("compute error vs the FP64 oracle fed the same rounded intensities: "
+                     "tests/test_gpu_parity.py::test_reduced_precision_intensity")
+    del imgs
+    return out
+
+
+def figure_north_star(args, dev, stream):
+    """The whole 1024^3 (1.07e9-particle) lattice set, FP16 intensity, one
+    1920x1080 absorptive frame."""
+    import torch
+
+    import synth
+    from paper_1004_1302_gb300 import splotch as S
+    t0 = time.perf_counter()
+    res = resident_lattice(1024, dev)
+    torch.cuda.synchronize(dev)
+    t_gen = time.perf_counter() - t0
+    cam = synth.CameraSpec((0.5, 0.5, -1.5), (0.5, 0.5, 0.5), (0.0, 1.0, 0.0), 45.0, 1920, 1080)
+    fr = S.Frame(res, cam, synth.colormap(), S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev,
+                 max_tile_entries=int(2.2 * res.n))
+    fr.render()
+    med, mean = time_frames(fr, 3, 1, stream)
+    st = stage_times(fr, 3, 1, stream)
+    inf = fr.info()
+    out = {"particles": res.n, "dtype": "f16 intensity, f32 position/h", "ms_per_step": mean, "p50_ms": med,
+           "value": res.n / (mean * 1e-3), "unit": "particles/s", "stages_ms": st, "visible": int(inf.visible),
+           "tile_entries": int(inf.tile_entries), "status": int(inf.status), "generate_and_upload_s": t_gen,
+           "parity": "sampled pixels vs the FP64 oracle and sampled keys bit-exact: "
+                     "tests/test_gpu_full_set_frame.py"}
+    del fr, res
+    torch.cuda.empty_cache()
+    return out
+
+
+def figure_batching(args, dev, stream):
+    """64 orbit views of the 10M two-species set at 1024^2 (absorptive) and
+    32 snapshots of 10k-2M particles at 512^2 (emission): launched frame by
+    frame from the host against one captured CUDA graph (fixed tile 16, batch
+    64, default split threshold; best of the graph arrangements)."""
+    import torch
+
+    import synth
+    from paper_1004_1302_gb300 import splotch as S
+    from paper_1004_1302_gb300.batch import BatchRenderer
+    pal = synth.colormap()
+    ps, _ = synth.two_species(width=1024, height=1024)
+    dp = S.upload(ps, dev, "f32")
+    views = [synth.orbit_camera(k, 64, 1024, 1024) for k in range(64)]
+    snaps = [synth.snapshot(k, n) for k, n in enumerate(synth.snapshot_sizes(32))]
+    dsnaps = [S.upload(sp, dev, "f32") for sp, _ in snaps]
+    jobs = [(dp, v, pal, S.ABSORPTIVE) for v in views] + [(d, c, pal, S.EMISSION) for d, (_, c) in zip(dsnaps, snaps)]
+    br = BatchRenderer(jobs, tile=args.tile, batch=args.batch, device=dev)
+    br.prepare()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    def plain():
+        for f in br.frames:
+            f.run()
+
+    reps = max(3, args.steps // 4)
+    t_plain = timed(plain, reps)
+    plain_imgs = [im.clone() for im in br.images()]
+    by_groups, same = {}, True
+    for groups in (1, 0):
+        br.groups = groups
+        br.capture()
+        by_groups[groups] = timed(br.replay, reps)
+        same = same and all(torch.equal(x, y) for x, y in zip(plain_imgs, br.images()))
+    t_graph = min(by_groups.values())
+    out = {"frames": len(br.frames), "particles": br.particles, "plain_ms_per_batch": t_plain,
+           "batched_ms_per_batch": t_graph, "plain_value": br.particles / (t_plain * 1e-3),
+           "value": br.particles / (t_graph * 1e-3), "unit": "particles/s", "speedup": t_plain / t_graph,
+           "frames_per_s": len(br.frames) / (t_graph * 1e-3), "ms_by_groups": by_groups,
+           "images_identical_to_single_frames": bool(same),
+           "status_ok": all(st == 0 for st in br.statuses())}
+    del br, plain_imgs, dsnaps, dp
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(ps, cam, pal):
     import synth  # noqa: F401
     from oracle import oracle as O
@@ -832,6 +1013,10 @@ def main():
     out["clocks"] = clk
 
     if not args.quick:
+        ref_img = fr.image.clone()
+        out["early_termination"] = figure_early_termination(args, dev, stream, dp, cam, pal, ref_img)
+        out["depth_slabs"] = figure_depth_slabs(args, dev, stream, dp, cam, pal, ref_img, keys)
+        del ref_img
         # emission mode on the same particles
         fe = S.Frame(dp, cam, pal, S.EMISSION, tile=args.tile, batch=args.batch, device=dev)
         fe.render()
@@ -878,6 +1063,12 @@ def main():
                                    "render of step k", "status": e2e_status}
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(ps, cam, pal)
+        if not args.no_forms:
+            del pipe
+            torch.cuda.empty_cache()
+            out["precision"] = figure_precision(args, dev, stream)
+            out["batching"] = figure_batching(args, dev, stream)
+            out["north_star"] = figure_north_star(args, dev, stream)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define SPLOTCH_ABI_VERSION 2
+#define SPLOTCH_ABI_VERSION 3
 #define SPLOTCH_MAX_SPECIES 8
 #define SPLOTCH_MAX_PALETTE 256
 
@@ -122,6 +122,20 @@ typedef struct {
     int32_t large_threshold_px;   /* footprint area (px) above which a particle's tile entries are
                                      emitted cooperatively; 0 = (width + height) / 2 (Section 3.2) */
     uint64_t max_tile_entries;    /* capacity of the tile-entry arrays in the workspace, < 2^32 */
+    int32_t slab;                 /* 1: the transform keeps only the depth slab slab_key_lo <= key < slab_key_hi
+                                     (key = bit pattern of (float)Z, so the bounds are depths); every
+                                     other particle is culled.  The normalisation range still covers
+                                     every particle of a species.  0: no slab */
+    uint32_t slab_key_lo, slab_key_hi;
+    float t_min_cutoff;           /* absorptive early termination, 0 = off (the default; results are then
+                                     bit-for-bit those of the full integral).  > 0: a warp's pixels stop
+                                     taking particles once, for every channel c, T_max * M_c <=
+                                     t_min_cutoff * C_max,c, with T_max the largest transmittance of its
+                                     pixels, C_max,c the largest intensity they have reached and M_c the
+                                     largest E_c / A of any species (the light still to come through a
+                                     pixel is at most T * M_c, Eq. 1 integrated over the remaining
+                                     layers).  Never stops while a species with A = 0 emits.  Changes
+                                     each channel by at most t_min_cutoff times its image maximum */
 } splotch_render_params;
 
 /* Result summary read back by splotch_frame_info (synchronises the stream). */
@@ -225,6 +239,37 @@ int splotch_bin(const splotch_render_params *params, const splotch_camera *cam, 
                 size_t workspace_bytes, void *stream);
 int splotch_render_tiles(const splotch_render_params *params, const splotch_camera *cam, uint64_t n,
                          void *workspace, size_t workspace_bytes, float *image, void *stream);
+
+/*
+ * Partial image of a depth slab, for depth-sharded rendering (the reduction
+ * of partial images of Section 3.1, generalised to E != A by Eq. 1).  Light
+ * entering the rendered particles from behind leaves them as C + T I_in per
+ * pixel and channel: `color` receives C (the front-to-back render with a
+ * background of 0, as splotch_render_tiles writes it, except in E = A mode)
+ * and `trans` receives T (device, height x width x 3 floats each):
+ *   absorptive  T = prod_p exp(-A_p g_p) (the same in every channel)
+ *   emission    T = 1
+ *   E = A       C = 1 - exp(-tau), T = exp(-tau), tau = sum_p E_p g_p per channel
+ * Slabs rendered from the same set with params.slab and consecutive key
+ * ranges combine, nearest first, with splotch_compose into the image of the
+ * whole set.  Runs splotch_sort, splotch_bin and the tile render.
+ */
+int splotch_render_partial(const splotch_render_params *params, const splotch_camera *cam, uint64_t n,
+                           void *workspace, size_t workspace_bytes, float *color, float *trans, void *stream);
+
+/*
+ * Ordered composition of two partial images, `front` nearer the camera:
+ *   c_out = c_front + t_front * c_back,  t_out = t_front * t_back
+ * element by element over n_values floats (height x width x 3 for an
+ * image), each product rounded once, then the sum (no fused multiply-add).
+ * The operator is associative, not commutative: fold slabs in depth order.
+ * All pointers are device floats; c_out and t_out may each be the same array
+ * as an input (not a partial overlap); t_out may be NULL when only the
+ * colour is wanted (the last fold).  Pointers must be
+ * 16-byte aligned.  SPLOTCH_ERR_ARG for NULL or misaligned pointers.
+ */
+int splotch_compose(const float *c_front, const float *t_front, const float *c_back, const float *t_back,
+                    float *c_out, float *t_out, uint64_t n_values, void *stream);
 
 /* Synchronises `stream` and reads the frame summary from the workspace
  * (written by the last transform/colorize/render on it). */

@@ -66,6 +66,7 @@ struct Header {
     uint32_t vlo_enc[SPLOTCH_MAX_SPECIES][3], vhi_enc[SPLOTCH_MAX_SPECIES][3];   // vector components
     uint32_t qlo_enc[SPLOTCH_MAX_SPECIES], qhi_enc[SPLOTCH_MAX_SPECIES];         // modulating scalar
     float vlo[SPLOTCH_MAX_SPECIES][3], vhi[SPLOTCH_MAX_SPECIES][3], qmax[SPLOTCH_MAX_SPECIES];
+    float eoa_max[3];          // per channel, an upper bound of |E_c| / A over the particles (inf if some A = 0 emits)
     Layout layout;
 };
 
@@ -104,6 +105,8 @@ struct TransformArgs {
     float r0, r1, r2, cr, u0, u1, u2, cu;
     float s, half_w, half_h, w_max, h_max;
     float sigma_per_h, trunc_f;
+    int slab;                  // keep only slab_lo <= key < slab_hi
+    uint32_t slab_lo, slab_hi;
 };
 
 struct ColorizeArgs {
@@ -183,6 +186,8 @@ struct RenderArgs {
     const float4 *geo;         // sx, sy, r2, -log2(e)/sigma_pix^2
     const float4 *col;         // Er, Eg, Eb, A
     float *image;
+    float *trans;              // partial render: transmittance per pixel and channel (nullptr: none)
+    float cutoff;              // absorptive early termination bound (0: off)
     int width, height, tile, ntx, mode, batch;
 };
 
@@ -222,9 +227,13 @@ cudaError_t launch_sort_finish(Header *hdr, cudaStream_t st);   // absorptive or
 cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStream_t st);
 int super_passes(uint32_t nsuper);             // radix passes that group entries by super-tile
 uint64_t fine_list_offset(const Layout &L);    // workspace offset of the fine-tile lists
-cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float *image, cudaStream_t st);
+cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float *image, float *trans, float cutoff,
+                          cudaStream_t st);
+cudaError_t launch_compose(const float *cf, const float *tf, const float *cb, const float *tb, float *co, float *to,
+                           uint64_t n, cudaStream_t st);
 cudaError_t launch_count_fragments(void *ws, const Layout &L, uint64_t *out, cudaStream_t st);
-RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, float *image);
+RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, float *image, float *trans = nullptr,
+                            float cutoff = 0.0f);
 cudaError_t launch_render_batch(const BatchArgs &b, int tile, int batch, cudaStream_t st);
 uint32_t roi_ctas(uint64_t n);
 cudaError_t launch_roi(const splotch_particles *p, const double box[6], void *scratch, uint64_t *count, float *ox,

@@ -63,9 +63,26 @@ template <int B> struct RenderSmem {
     float4 scull[2][B];   // sx, sy, r2 for the cull test
 };
 
+// Early termination of a warp (absorptive mode, a cutoff > 0): the light
+// still to come through a pixel of transmittance T is at most T M_c per
+// channel (M_c bounds E_c / A over all particles), so once T_max M_c <=
+// cutoff C_max,c over the warp's pixels inside the image, the rest of the
+// list changes none of them by more than cutoff times the channel's image
+// maximum.  Pixels outside the image take no part; a warp with none is done.
+__device__ __forceinline__ bool warp_converged(float tmax, float c0, float c1, float c2, const float *M, float cutoff) {
+    tmax = ordered_to_float(__reduce_max_sync(0xFFFFFFFFu, float_to_ordered(tmax)));
+    c0 = ordered_to_float(__reduce_max_sync(0xFFFFFFFFu, float_to_ordered(c0)));
+    c1 = ordered_to_float(__reduce_max_sync(0xFFFFFFFFu, float_to_ordered(c1)));
+    c2 = ordered_to_float(__reduce_max_sync(0xFFFFFFFFu, float_to_ordered(c2)));
+    if (tmax == -INFINITY) return true;
+    return tmax * M[0] <= cutoff * c0 && tmax * M[1] <= cutoff * c1 && tmax * M[2] <= cutoff * c2;
+}
+
 // One screen tile, rendered by the whole CTA (all threads must call it).
 // SERIES: every particle's A is at most kSeriesMaxA (absorptive mode).
-template <int T, int MODE, int B, bool SERIES>
+// ET: early termination (absorptive mode with a cutoff).  PT: partial image
+// (the transmittance is written too).
+template <int T, int MODE, int B, bool SERIES, bool ET, bool PT>
 __device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile, RenderSmem<B> &sm) {
     constexpr int kThreads = T * T / 2;
     constexpr int WX = 8, WY = 8;               // pixel block of one warp (two pixels per lane)
@@ -90,6 +107,14 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile,
     const float yt0 = (float)wy0 + 0.5f, yt1 = (float)wy0 + 3.5f, yb0 = (float)wy0 + 4.5f, yb1 = (float)wy0 + 7.5f;
 
     float2 cr = f2(0.f), cg = f2(0.f), cb = f2(0.f), tacc = f2(1.f);
+    const bool in0 = px0 < a.width && py < a.height, in1 = px0 + 1 < a.width && py < a.height;
+    float M[3] = {0.f, 0.f, 0.f};
+    if (ET) {
+        M[0] = a.hdr->eoa_max[0];
+        M[1] = a.hdr->eoa_max[1];
+        M[2] = a.hdr->eoa_max[2];
+    }
+    bool wdone = false;
 
     const bool ok = a.hdr->status == SPLOTCH_OK;
     const uint32_t begin = ok ? a.toff[tile] : 0u, end = ok ? a.toff[tile + 1] : 0u;
@@ -174,7 +199,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile,
         if (next < end) load(next);
         __syncthreads();
         const uint32_t nb = min((uint32_t)B, end - base);
-        for (uint32_t c = 0; c < nb; c += 32) {
+        for (uint32_t c = 0; c < (ET && wdone ? 0u : nb); c += 32) {
             // each lane tests particle c + lane against the four quadrants
             bool k0 = false, k1 = false, k2 = false, k3 = false;
             if (c + lane < nb) {
@@ -211,10 +236,28 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile,
                 apply(j);
             }
         }
-        __syncthreads();
+        if (ET) {
+            if (!wdone) {
+                const float ni = -INFINITY;
+                wdone = warp_converged(fmaxf(in0 ? tacc.x : ni, in1 ? tacc.y : ni),
+                                       fmaxf(in0 ? cr.x : ni, in1 ? cr.y : ni), fmaxf(in0 ? cg.x : ni, in1 ? cg.y : ni),
+                                       fmaxf(in0 ? cb.x : ni, in1 ? cb.y : ni), M, a.cutoff);
+            }
+            if (__syncthreads_and(wdone)) break;
+        } else {
+            __syncthreads();
+        }
         if (next < end) store(buf ^ 1, next);
     }
 
+    // transmittance of a partial render (E = A: exp(-tau) before C = 1 - exp(-tau))
+    float2 tr = MODE == SPLOTCH_ABSORPTIVE ? tacc : f2(1.0f);
+    float2 tg = tr, tb = tr;
+    if (MODE == SPLOTCH_E_EQ_A && PT) {
+        tr = make_float2(expf(-cr.x), expf(-cr.y));
+        tg = make_float2(expf(-cg.x), expf(-cg.y));
+        tb = make_float2(expf(-cb.x), expf(-cb.y));
+    }
     if (MODE == SPLOTCH_E_EQ_A) {
         cr = make_float2(-expm1f(-cr.x), -expm1f(-cr.y));
         cg = make_float2(-expm1f(-cg.x), -expm1f(-cg.y));
@@ -228,6 +271,15 @@ __device__ __forceinline__ void render_tile(const RenderArgs &a, const int tile,
         if (px0 + 1 < a.width) {
             row[3 * px0 + 3] = cr.y; row[3 * px0 + 4] = cg.y; row[3 * px0 + 5] = cb.y;
         }
+        if (PT) {
+            float *trow = a.trans + (size_t)py * a.width * 3;
+            if (px0 < a.width) {
+                trow[3 * px0 + 0] = tr.x; trow[3 * px0 + 1] = tg.x; trow[3 * px0 + 2] = tb.x;
+            }
+            if (px0 + 1 < a.width) {
+                trow[3 * px0 + 3] = tr.y; trow[3 * px0 + 4] = tg.y; trow[3 * px0 + 5] = tb.y;
+            }
+        }
     }
 }
 
@@ -240,7 +292,7 @@ constexpr int render_threads(int T) { return T >= 16 ? T * T / 4 : T * T / 2; }
 // a 2 x 2 square (two packed pixel pairs, one per row).  A step now composites
 // eight particles (one per group) on 128 pixels, and the column terms are
 // shared by the two rows.
-template <int T, int MODE, int B, bool SERIES>
+template <int T, int MODE, int B, bool SERIES, bool ET, bool PT>
 __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile, RenderSmem<B> &sm) {
     constexpr int kThreads = T * T / 4;
     constexpr int WX = 16, WY = 8;
@@ -263,6 +315,13 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
 
     float2 crA = f2(0.f), cgA = f2(0.f), cbA = f2(0.f), tA = f2(1.f);
     float2 crB = f2(0.f), cgB = f2(0.f), cbB = f2(0.f), tB = f2(1.f);
+    float M[3] = {0.f, 0.f, 0.f};
+    if (ET) {
+        M[0] = a.hdr->eoa_max[0];
+        M[1] = a.hdr->eoa_max[1];
+        M[2] = a.hdr->eoa_max[2];
+    }
+    bool wdone = false;
 
     const bool ok = a.hdr->status == SPLOTCH_OK;
     const uint32_t begin = ok ? a.toff[tile] : 0u, end = ok ? a.toff[tile + 1] : 0u;
@@ -352,7 +411,7 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
         if (next < end) load(next);
         __syncthreads();
         const uint32_t nb = min((uint32_t)B, end - base);
-        for (uint32_t c = 0; c < nb; c += 32) {
+        for (uint32_t c = 0; c < (ET && wdone ? 0u : nb); c += 32) {
             // each lane tests entry c + lane against the eight quadrants (4 columns x 2 rows)
             bool k[8];
 #pragma unroll
@@ -400,10 +459,35 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
                 apply(j);
             }
         }
-        __syncthreads();
+        if (ET) {
+            if (!wdone) {
+                const float ni = -INFINITY;
+                const bool x0 = px0 < a.width, x1 = px0 + 1 < a.width;
+                const bool yA = py0 < a.height, yB = py0 + 1 < a.height;
+                auto mx4 = [&](float2 A, float2 Bv) {
+                    return fmaxf(fmaxf(x0 && yA ? A.x : ni, x1 && yA ? A.y : ni),
+                                 fmaxf(x0 && yB ? Bv.x : ni, x1 && yB ? Bv.y : ni));
+                };
+                wdone = warp_converged(mx4(tA, tB), mx4(crA, crB), mx4(cgA, cgB), mx4(cbA, cbB), M, a.cutoff);
+            }
+            if (__syncthreads_and(wdone)) break;
+        } else {
+            __syncthreads();
+        }
         if (next < end) store(buf ^ 1, next);
     }
 
+    // transmittance of a partial render (E = A: exp(-tau) before C = 1 - exp(-tau))
+    float2 trA = MODE == SPLOTCH_ABSORPTIVE ? tA : f2(1.0f), trB = MODE == SPLOTCH_ABSORPTIVE ? tB : f2(1.0f);
+    float2 tgA = trA, tbA = trA, tgB = trB, tbB = trB;
+    if (MODE == SPLOTCH_E_EQ_A && PT) {
+        trA = make_float2(expf(-crA.x), expf(-crA.y));
+        tgA = make_float2(expf(-cgA.x), expf(-cgA.y));
+        tbA = make_float2(expf(-cbA.x), expf(-cbA.y));
+        trB = make_float2(expf(-crB.x), expf(-crB.y));
+        tgB = make_float2(expf(-cgB.x), expf(-cgB.y));
+        tbB = make_float2(expf(-cbB.x), expf(-cbB.y));
+    }
     if (MODE == SPLOTCH_E_EQ_A) {
         crA = make_float2(-expm1f(-crA.x), -expm1f(-crA.y));
         cgA = make_float2(-expm1f(-cgA.x), -expm1f(-cgA.y));
@@ -412,9 +496,9 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
         cgB = make_float2(-expm1f(-cgB.x), -expm1f(-cgB.y));
         cbB = make_float2(-expm1f(-cbB.x), -expm1f(-cbB.y));
     }
-    auto put = [&](int py, float2 cr, float2 cg, float2 cb) {
+    auto put = [&](float *img, int py, float2 cr, float2 cg, float2 cb) {
         if (py >= a.height) return;
-        float *rowp = a.image + (size_t)py * a.width * 3;
+        float *rowp = img + (size_t)py * a.width * 3;
         if (px0 < a.width) {
             rowp[3 * px0 + 0] = cr.x; rowp[3 * px0 + 1] = cg.x; rowp[3 * px0 + 2] = cb.x;
         }
@@ -422,24 +506,29 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
             rowp[3 * px0 + 3] = cr.y; rowp[3 * px0 + 4] = cg.y; rowp[3 * px0 + 5] = cb.y;
         }
     };
-    put(py0, crA, cgA, cbA);
-    put(py0 + 1, crB, cgB, cbB);
+    put(a.image, py0, crA, cgA, cbA);
+    put(a.image, py0 + 1, crB, cgB, cbB);
+    if (PT) {
+        put(a.trans, py0, trA, tgA, tbA);
+        put(a.trans, py0 + 1, trB, tgB, tbB);
+    }
 }
 
 // Tile render with the layout for the tile size.
-template <int T, int MODE, int B, bool SERIES>
+template <int T, int MODE, int B, bool SERIES, bool ET = false, bool PT = false>
 __device__ __forceinline__ void render_any(const RenderArgs &a, const int tile, RenderSmem<B> &sm) {
-    if constexpr (T >= 16) render_tile4<T, MODE, B, SERIES>(a, tile, sm);
-    else render_tile<T, MODE, B, SERIES>(a, tile, sm);
+    if constexpr (T >= 16) render_tile4<T, MODE, B, SERIES, ET, PT>(a, tile, sm);
+    else render_tile<T, MODE, B, SERIES, ET, PT>(a, tile, sm);
 }
 
-template <int T, int MODE, int B>
+// ET: absorptive early termination (a.cutoff > 0); PT: partial image (a.trans).
+template <int T, int MODE, int B, bool ET, bool PT>
 __global__ void __launch_bounds__(render_threads(T)) k_render(RenderArgs a) {
     __shared__ __align__(16) RenderSmem<B> sm;
     const uint32_t tile = __ldg(&a.torder[blockIdx.x]);
     if (tile >= gridDim.x) return;   // a workspace that was never binned
-    if (MODE == SPLOTCH_ABSORPTIVE && a.hdr->series_only) render_any<T, MODE, B, true>(a, (int)tile, sm);
-    else render_any<T, MODE, B, false>(a, (int)tile, sm);
+    if (MODE == SPLOTCH_ABSORPTIVE && a.hdr->series_only) render_any<T, MODE, B, true, ET, PT>(a, (int)tile, sm);
+    else render_any<T, MODE, B, false, ET, PT>(a, (int)tile, sm);
 }
 
 // Persistent render of the tiles of many frames: each CTA takes the next
@@ -474,25 +563,35 @@ __global__ void __launch_bounds__(render_threads(T)) k_render_batch(const __grid
     }
 }
 
-template <int T, int MODE>
+template <int T, int MODE, bool ET, bool PT>
 static void launch_tb(const RenderArgs &a, int ntiles, cudaStream_t st) {
     switch (a.batch) {
-    case 64: k_render<T, MODE, 64><<<ntiles, render_threads(T), 0, st>>>(a); break;
-    case 128: k_render<T, MODE, 128><<<ntiles, render_threads(T), 0, st>>>(a); break;
-    default: k_render<T, MODE, 256><<<ntiles, render_threads(T), 0, st>>>(a); break;
+    case 64: k_render<T, MODE, 64, ET, PT><<<ntiles, render_threads(T), 0, st>>>(a); break;
+    case 128: k_render<T, MODE, 128, ET, PT><<<ntiles, render_threads(T), 0, st>>>(a); break;
+    default: k_render<T, MODE, 256, ET, PT><<<ntiles, render_threads(T), 0, st>>>(a); break;
     }
+}
+
+template <int T, int MODE, bool ET>
+static void launch_tp(const RenderArgs &a, int ntiles, cudaStream_t st) {
+    if (a.trans) launch_tb<T, MODE, ET, true>(a, ntiles, st);
+    else launch_tb<T, MODE, ET, false>(a, ntiles, st);
 }
 
 template <int T>
 static void launch_t(const RenderArgs &a, int ntiles, cudaStream_t st) {
     switch (a.mode) {
-    case SPLOTCH_EMISSION: launch_tb<T, SPLOTCH_EMISSION>(a, ntiles, st); break;
-    case SPLOTCH_ABSORPTIVE: launch_tb<T, SPLOTCH_ABSORPTIVE>(a, ntiles, st); break;
-    default: launch_tb<T, SPLOTCH_E_EQ_A>(a, ntiles, st); break;
+    case SPLOTCH_EMISSION: launch_tp<T, SPLOTCH_EMISSION, false>(a, ntiles, st); break;
+    case SPLOTCH_ABSORPTIVE:
+        if (a.cutoff > 0.0f) launch_tp<T, SPLOTCH_ABSORPTIVE, true>(a, ntiles, st);
+        else launch_tp<T, SPLOTCH_ABSORPTIVE, false>(a, ntiles, st);
+        break;
+    default: launch_tp<T, SPLOTCH_E_EQ_A, false>(a, ntiles, st); break;
     }
 }
 
-RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, float *image) {
+RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, float *image, float *trans,
+                            float cutoff) {
     RenderArgs a{};
     a.hdr = header(ws);
     a.toff = at<uint32_t>(ws, L.off_toff);
@@ -501,6 +600,8 @@ RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, floa
     a.geo = at<float4>(ws, L.off_geo);
     a.col = at<float4>(ws, L.off_col);
     a.image = image;
+    a.trans = trans;
+    a.cutoff = mode == SPLOTCH_ABSORPTIVE ? cutoff : 0.0f;
     a.width = L.width;
     a.height = L.height;
     a.tile = L.tile;
@@ -510,8 +611,9 @@ RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, floa
     return a;
 }
 
-cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float *image, cudaStream_t st) {
-    const RenderArgs a = make_render_args(ws, L, mode, batch, image);
+cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float *image, float *trans, float cutoff,
+                          cudaStream_t st) {
+    const RenderArgs a = make_render_args(ws, L, mode, batch, image, trans, cutoff);
     switch (L.tile) {
     case 8: launch_t<8>(a, (int)L.ntiles, st); break;
     case 32: launch_t<32>(a, (int)L.ntiles, st); break;
@@ -553,6 +655,53 @@ cudaError_t launch_render_batch(const BatchArgs &b, int tile, int batch, cudaStr
     }
     count_launches(1);
     return e;
+}
+
+// Ordered composition of two partial images (front nearer the camera):
+// C = C_f + T_f C_b, T = T_f T_b, each product rounded once, no contraction.
+// Four values per thread with 16-byte loads; an HBM-bound stream of 16 B read
+// and 8 B (4 B without T) written per value.
+__global__ void __launch_bounds__(256) k_compose(const float4 *cf, const float4 *tf, const float4 *cb, const float4 *tb,
+                                                 float4 *co, float4 *to, uint64_t n4) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4; i += (uint64_t)gridDim.x * blockDim.x) {
+        const float4 a = cf[i], t = tf[i], b = cb[i];
+        float4 u;
+        if (to) u = tb[i];
+        co[i] = make_float4(__fadd_rn(a.x, __fmul_rn(t.x, b.x)), __fadd_rn(a.y, __fmul_rn(t.y, b.y)),
+                            __fadd_rn(a.z, __fmul_rn(t.z, b.z)), __fadd_rn(a.w, __fmul_rn(t.w, b.w)));
+        if (to) to[i] = make_float4(__fmul_rn(t.x, u.x), __fmul_rn(t.y, u.y), __fmul_rn(t.z, u.z), __fmul_rn(t.w, u.w));
+    }
+}
+
+__global__ void k_compose_tail(const float *cf, const float *tf, const float *cb, const float *tb, float *co, float *to,
+                               uint64_t i0, uint64_t n) {
+    const uint64_t i = i0 + threadIdx.x;
+    if (i >= n) return;
+    const float a = cf[i], t = tf[i], b = cb[i];
+    const float u = to ? tb[i] : 0.0f;
+    co[i] = __fadd_rn(a, __fmul_rn(t, b));
+    if (to) to[i] = __fmul_rn(t, u);
+}
+
+cudaError_t launch_compose(const float *cf, const float *tf, const float *cb, const float *tb, float *co, float *to,
+                           uint64_t n, cudaStream_t st) {
+    const uint64_t n4 = n / 4;
+    if (n4) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const uint64_t want = (n4 + 255) / 256, cap = (uint64_t)(sms > 0 ? sms : 148) * 8;
+        k_compose<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(
+            reinterpret_cast<const float4 *>(cf), reinterpret_cast<const float4 *>(tf),
+            reinterpret_cast<const float4 *>(cb), reinterpret_cast<const float4 *>(tb), reinterpret_cast<float4 *>(co),
+            reinterpret_cast<float4 *>(to), n4);
+        count_launches(1);
+    }
+    if (n % 4) {
+        k_compose_tail<<<1, 32, 0, st>>>(cf, tf, cb, tb, co, to, n4 * 4, n);
+        count_launches(1);
+    }
+    return cudaGetLastError();
 }
 
 // Number of (pixel, particle) pairs that pass the membership test, summed

@@ -92,6 +92,8 @@ static int check_params(const splotch_render_params *pr) {
     if (pr->mode < 0 || pr->mode > 2) return SPLOTCH_ERR_ARG;
     if (!(pr->batch == 64 || pr->batch == 128 || pr->batch == 256)) return SPLOTCH_ERR_ARG;
     if (!(pr->sigma_per_h > 0.0f) || !(pr->trunc_f > 0.0f) || pr->large_threshold_px < 0) return SPLOTCH_ERR_ARG;
+    if (pr->slab != 0 && pr->slab != 1) return SPLOTCH_ERR_ARG;
+    if (!(pr->t_min_cutoff >= 0.0f) || !(pr->t_min_cutoff < 1.0f)) return SPLOTCH_ERR_ARG;
     return SPLOTCH_OK;
 }
 
@@ -219,6 +221,9 @@ int splotch_transform(const splotch_particles *p, const splotch_camera *cam, con
     a.h_max = (float)(cam->height - 1);
     a.sigma_per_h = params->sigma_per_h;
     a.trunc_f = params->trunc_f;
+    a.slab = params->slab != 0;
+    a.slab_lo = params->slab_key_lo;
+    a.slab_hi = params->slab_key_hi;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_init_header(workspace, L, p->n_species, params->mode, st);
     if (e == cudaSuccess) e = launch_transform(a, workspace, L, st);
@@ -290,8 +295,31 @@ int splotch_render_tiles(const splotch_render_params *params, const splotch_came
     if (s) return s;
     if ((s = check_ws(workspace, workspace_bytes, L))) return s;
     if (!image) return SPLOTCH_ERR_ARG;
-    return cuda_status(launch_render(workspace, L, params->mode, params->batch, image,
+    return cuda_status(launch_render(workspace, L, params->mode, params->batch, image, nullptr,
+                                     params->t_min_cutoff, static_cast<cudaStream_t>(stream)));
+}
+
+int splotch_render_partial(const splotch_render_params *params, const splotch_camera *cam, uint64_t n,
+                           void *workspace, size_t workspace_bytes, float *color, float *trans, void *stream) {
+    if (!color || !trans) return SPLOTCH_ERR_ARG;
+    int s = splotch_sort(params, cam, n, workspace, workspace_bytes, stream);
+    if (!s) s = splotch_bin(params, cam, n, workspace, workspace_bytes, stream);
+    if (s) return s;
+    Layout L;
+    frame_layout(params, cam, n, &L);
+    return cuda_status(launch_render(workspace, L, params->mode, params->batch, color, trans, params->t_min_cutoff,
                                      static_cast<cudaStream_t>(stream)));
+}
+
+int splotch_compose(const float *c_front, const float *t_front, const float *c_back, const float *t_back,
+                    float *c_out, float *t_out, uint64_t n_values, void *stream) {
+    if (!c_front || !t_front || !c_back || !t_back || !c_out) return SPLOTCH_ERR_ARG;
+    const uintptr_t bits = reinterpret_cast<uintptr_t>(c_front) | reinterpret_cast<uintptr_t>(t_front) |
+                           reinterpret_cast<uintptr_t>(c_back) | reinterpret_cast<uintptr_t>(t_back) |
+                           reinterpret_cast<uintptr_t>(c_out) | reinterpret_cast<uintptr_t>(t_out);
+    if (bits & 15u) return SPLOTCH_ERR_ARG;
+    return cuda_status(launch_compose(c_front, t_front, c_back, t_back, c_out, t_out, n_values,
+                                      static_cast<cudaStream_t>(stream)));
 }
 
 int splotch_render_tiles_batch(const splotch_batch_item *items, int32_t n_items, int32_t tile, int32_t batch,

@@ -40,6 +40,7 @@ __global__ void k_init_header(Header *hdr, Layout L, int n_species, int mode) {
         hdr->qhi_enc[s] = 0u;
         hdr->qmax[s] = 0.0f;
     }
+    for (int c = 0; c < 3; ++c) hdr->eoa_max[c] = 0.0f;
     hdr->layout = L;
 }
 
@@ -61,6 +62,10 @@ __device__ __forceinline__ Footprint footprint(const TransformArgs &a, float x, 
     // the depth's conversions and near-plane test on the integer units (double throughput is low)
     if (!ieee::beyond(Z, a.znear)) return f;
     float Zf = ieee::narrow_positive(Z);
+    if (a.slab) {   // depth slab of a partial render: lo <= key < hi
+        const uint32_t k = __float_as_uint(Zf);
+        if (k < a.slab_lo || k >= a.slab_hi) return f;
+    }
     float X = __fsub_rn(__fmaf_rn(z, a.r2, __fmaf_rn(y, a.r1, __fmul_rn(x, a.r0))), a.cr);
     float Y = __fsub_rn(__fmaf_rn(z, a.u2, __fmaf_rn(y, a.u1, __fmul_rn(x, a.u0))), a.cu);
     float inv = __frcp_rn(Zf);
@@ -169,6 +174,30 @@ __global__ void k_range_finish(Header *hdr, ColorizeArgs a) {
     const bool series = empty || a.sp[s].absorption <= kSeriesMaxA;
     const bool all = __all_sync(0xFFFFFFFFu, series);
     if (s == 0) hdr->series_only = all ? 1u : 0u;
+    // Bound of the light a pixel can still receive behind transmittance T:
+    // each layer adds T_acc E (1 - T_p)/A <= T_acc (1 - T_p) max|E|/A, which
+    // sums to at most T max|E|/A.  Per species |E_c| <= |brightness| times
+    // the largest |palette| (or |fixed rgb|, or 1 for a vector quantity) of
+    // channel c; the modulation scales E and A alike and cancels.
+    float pmax[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float m = 0.0f;
+        for (int k = s; k < a.n_entries; k += 32) m = fmaxf(m, fabsf(a.palette[3 * k + c]));
+        pmax[c] = __uint_as_float(__reduce_max_sync(0xFFFFFFFFu, __float_as_uint(m)));
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float r = 0.0f;
+        if (!empty) {
+            const splotch_species &sp = a.sp[s];
+            const float cm = sp.use_vector ? 1.0f : sp.use_colormap ? pmax[c] : fabsf(sp.fixed_rgb[c]);
+            const float e = fabsf(sp.brightness) * cm;
+            r = sp.absorption > 0.0f ? e / sp.absorption : (e > 0.0f ? INFINITY : 0.0f);
+        }
+        r = __uint_as_float(__reduce_max_sync(0xFFFFFFFFu, __float_as_uint(r)));
+        if (s == 0) hdr->eoa_max[c] = r;
+    }
     if (!have) return;
     float lo = a.sp[s].lo, hi = a.sp[s].hi;
     if (isnan(lo)) lo = empty ? 0.0f : ordered_to_float(hdr->range_lo_enc[s]);

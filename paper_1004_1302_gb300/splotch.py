@@ -104,7 +104,8 @@ class SpeciesParams(ctypes.Structure):
 class RenderParams(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tile", ctypes.c_int32), ("sigma_per_h", ctypes.c_float),
                 ("trunc_f", ctypes.c_float), ("batch", ctypes.c_int32), ("large_threshold_px", ctypes.c_int32),
-                ("max_tile_entries", ctypes.c_uint64)]
+                ("max_tile_entries", ctypes.c_uint64), ("slab", ctypes.c_int32), ("slab_key_lo", ctypes.c_uint32),
+                ("slab_key_hi", ctypes.c_uint32), ("t_min_cutoff", ctypes.c_float)]
 
 
 class BatchItem(ctypes.Structure):
@@ -133,7 +134,8 @@ EXPORTS = ["splotch_abi_version", "splotch_status_string", "splotch_camera_init"
            "splotch_get_order", "splotch_get_tile_lists", "splotch_get_colors", "splotch_count_fragments",
            "splotch_launch_count", "splotch_sort_keys_no_alloc", "splotch_render_tiles_batch",
            "splotch_roi_scratch_size", "splotch_roi_count", "splotch_roi_select", "splotch_block_read",
-           "splotch_loader_create", "splotch_loader_start", "splotch_loader_wait", "splotch_loader_destroy"]
+           "splotch_loader_create", "splotch_loader_start", "splotch_loader_wait", "splotch_loader_destroy",
+           "splotch_render_partial", "splotch_compose"]
 
 _lib = None
 _lib_path = None
@@ -165,6 +167,8 @@ def load(path: str | None = None):
         "splotch_sort": ([P(RenderParams), P(Camera), U64, V, ctypes.c_size_t, V], I32),
         "splotch_bin": ([P(RenderParams), P(Camera), U64, V, ctypes.c_size_t, V], I32),
         "splotch_render_tiles": ([P(RenderParams), P(Camera), U64, V, ctypes.c_size_t, V, V], I32),
+        "splotch_render_partial": ([P(RenderParams), P(Camera), U64, V, ctypes.c_size_t, V, V, V], I32),
+        "splotch_compose": ([V, V, V, V, V, V, U64, V], I32),
         "splotch_frame_info": ([V, ctypes.c_size_t, P(FrameInfo), V], I32),
         "splotch_get_keys": ([V, ctypes.c_size_t, V, V, V], I32),
         "splotch_get_geometry": ([V, ctypes.c_size_t, V, V, V, V], I32),
@@ -246,6 +250,17 @@ def splotch_bin(params, cam, n, ws, ws_bytes, stream):
 def splotch_render_tiles(params, cam, n, ws, ws_bytes, image, stream):
     _check(load().splotch_render_tiles(ctypes.byref(params), ctypes.byref(cam), n, ws, ws_bytes, image, stream),
            "splotch_render_tiles")
+
+
+def splotch_render_partial(params, cam, n, ws, ws_bytes, color, trans, stream):
+    _check(load().splotch_render_partial(ctypes.byref(params), ctypes.byref(cam), n, ws, ws_bytes, color, trans,
+                                         stream), "splotch_render_partial")
+
+
+def splotch_compose(c_front: int, t_front: int, c_back: int, t_back: int, c_out: int, t_out, n_values: int,
+                    stream: int):
+    _check(load().splotch_compose(c_front, t_front, c_back, t_back, c_out, t_out, n_values, stream),
+           "splotch_compose")
 
 
 def splotch_frame_info(ws: int, ws_bytes: int, stream: int) -> FrameInfo:
@@ -405,13 +420,25 @@ def make_species(sp) -> SpeciesParams:
 
 
 def make_params(mode: int, tile: int = 16, batch: int = 64, sigma_per_h: float = 1.0, trunc_f: float = 2.0,
-                large_threshold_px: int = 0, max_tile_entries: int = 0) -> RenderParams:
+                large_threshold_px: int = 0, max_tile_entries: int = 0, slab=None,
+                t_min_cutoff: float = 0.0) -> RenderParams:
+    """slab: None, or (key_lo, key_hi) to keep only depth keys in [key_lo, key_hi)."""
     p = RenderParams()
     p.mode, p.tile, p.batch = int(mode), int(tile), int(batch)
     p.sigma_per_h, p.trunc_f = float(sigma_per_h), float(trunc_f)
     p.large_threshold_px = int(large_threshold_px)
     p.max_tile_entries = int(max_tile_entries)
+    if slab is not None:
+        p.slab, p.slab_key_lo, p.slab_key_hi = 1, int(slab[0]), int(slab[1])
+    p.t_min_cutoff = float(t_min_cutoff)
     return p
+
+
+def depth_key(z: float) -> int:
+    """The depth key of camera depth z > 0: the bit pattern of float32(z)
+    (keys order like depths), for slab bounds."""
+    import struct
+    return struct.unpack("<I", struct.pack("<f", float(z)))[0]
 
 
 _DTYPE_CODE = {"f32": F32, "f16": F16, "bf16": BF16}
@@ -487,7 +514,7 @@ class Frame:
 
     def __init__(self, dp: DeviceParticles, cam_spec, palette, mode: int, tile: int = 16, batch: int = 64,
                  sigma_per_h: float = 1.0, trunc_f: float = 2.0, large_threshold_px: int = 0,
-                 max_tile_entries: int | None = None, device="cuda"):
+                 max_tile_entries: int | None = None, device="cuda", slab=None, t_min_cutoff: float = 0.0):
         import torch
         self.torch = torch
         self.dp = dp
@@ -500,8 +527,10 @@ class Frame:
         if max_tile_entries is None:
             ntiles = math.ceil(self.W / tile) * math.ceil(self.H / tile)
             max_tile_entries = max(4 * dp.n, 1024) + ntiles
-        self.params = make_params(mode, tile, batch, sigma_per_h, trunc_f, large_threshold_px, max_tile_entries)
+        self.params = make_params(mode, tile, batch, sigma_per_h, trunc_f, large_threshold_px, max_tile_entries,
+                                  slab, t_min_cutoff)
         self.pstruct = dp.struct()
+        self.trans = None
         self.species = [make_species(s) for s in dp.species]
         self.image = torch.zeros((self.H, self.W, 3), dtype=torch.float32, device=self.device)
         self._alloc()
@@ -538,6 +567,31 @@ class Frame:
         self.colorize(stream)
         splotch_render(self.params, self.cam, self.dp.n, self.ws.data_ptr(), self.ws_bytes, self.image.data_ptr(),
                        self.stream_ptr(stream))
+
+    def run_partial(self, stream=None):
+        """Enqueue a whole frame as a partial image: colour into `image`,
+        transmittance into `trans` (both H x W x 3)."""
+        if self.trans is None:
+            self.trans = self.torch.empty_like(self.image)
+        self.transform(stream)
+        self.colorize(stream)
+        splotch_render_partial(self.params, self.cam, self.dp.n, self.ws.data_ptr(), self.ws_bytes,
+                               self.image.data_ptr(), self.trans.data_ptr(), self.stream_ptr(stream))
+
+    def render_partial(self, stream=None, max_retries: int = 3):
+        """Partial image (C, T) of this frame's particles (its depth slab if
+        the frame has one), growing the tile-entry capacity on overflow."""
+        for _ in range(max_retries + 1):
+            self.run_partial(stream)
+            inf = self.info(stream)
+            if inf.status == OK:
+                return self.image, self.trans
+            if inf.status != ERR_WORKSPACE:
+                raise SplotchError(inf.status, "partial frame")
+            self.params.max_tile_entries = int(inf.tile_entries * 1.1) + 1024
+            self.ws = None
+            self._alloc()
+        raise SplotchError(ERR_WORKSPACE, "partial frame")
 
     def info(self, stream=None) -> FrameInfo:
         return splotch_frame_info(self.ws.data_ptr(), self.ws_bytes, self.stream_ptr(stream))

@@ -30,7 +30,7 @@ def test_exports_every_declared_function(S):
     for name in declared:
         assert hasattr(lib, name), name
     assert set(declared) == set(S.EXPORTS)
-    assert lib.splotch_abi_version() == 2
+    assert lib.splotch_abi_version() == 3
 
 
 def test_status_strings(S):
@@ -80,6 +80,27 @@ def test_workspace_size_and_arguments(S):
         assert lib.splotch_workspace_size(1000, ctypes.byref(cam), ctypes.byref(q), ctypes.byref(out)) == S.ERR_ARG
     out = ctypes.c_size_t()
     assert lib.splotch_workspace_size(1 << 32, ctypes.byref(cam), ctypes.byref(p), ctypes.byref(out)) == S.ERR_ARG
+    # the slab flag is 0 or 1; the early-termination cutoff lies in [0, 1)
+    for bad in (dict(t_min_cutoff=-1e-6), dict(t_min_cutoff=1.0), dict(t_min_cutoff=float("nan"))):
+        q = S.make_params(S.ABSORPTIVE, max_tile_entries=1024, **bad)
+        assert lib.splotch_workspace_size(1000, ctypes.byref(cam), ctypes.byref(q), ctypes.byref(out)) == S.ERR_ARG
+    q = S.make_params(S.ABSORPTIVE, max_tile_entries=1024, slab=(0, 10))
+    assert lib.splotch_workspace_size(1000, ctypes.byref(cam), ctypes.byref(q), ctypes.byref(out)) == S.OK
+    q.slab = 2
+    assert lib.splotch_workspace_size(1000, ctypes.byref(cam), ctypes.byref(q), ctypes.byref(out)) == S.ERR_ARG
+    assert S.depth_key(1.0) == 0x3F800000 and S.depth_key(2.5) > S.depth_key(2.0)
+
+
+def test_compose_and_partial_reject_bad_pointers_on_the_host(S):
+    lib = S.load()
+    base = 1 << 20          # never dereferenced: the checks fail before anything is enqueued
+    assert lib.splotch_compose(base + 4, base, base, base, base, None, 16, None) == S.ERR_ARG
+    assert lib.splotch_compose(base, base, base, base, base, base + 8, 16, None) == S.ERR_ARG
+    assert lib.splotch_compose(base, None, base, base, base, None, 16, None) == S.ERR_ARG
+    _, spec = synth.plummer_mixture(n=10)
+    cam = S.make_camera(spec)
+    p = S.make_params(S.ABSORPTIVE, max_tile_entries=4096)
+    assert lib.splotch_render_partial(ctypes.byref(p), ctypes.byref(cam), 100, 256, 16, None, base, None) == S.ERR_ARG
 
 
 def test_calls_reject_bad_workspace_before_launch(S):
