@@ -54,6 +54,41 @@ __device__ __forceinline__ void bin_range(uint32_t ctas, uint32_t n, uint64_t *b
     if (*beg > *end) *beg = *end;
 }
 
+// Tile box from the depth sort's payload (8 bits per edge).
+__device__ __forceinline__ ushort4 unpack_tile_box(uint32_t v) {
+    return make_ushort4((unsigned short)(v & 0xFFu), (unsigned short)((v >> 8) & 0xFFu),
+                        (unsigned short)((v >> 16) & 0xFFu), (unsigned short)(v >> 24));
+}
+
+// Count pass when the tile boxes came through the depth sort in render
+// order: a sequential read, four boxes per thread at a time.
+__global__ void __launch_bounds__(256) k_bin_reduce_pay(BinArgs a) {
+    __shared__ unsigned long long ws[9];
+    const uint32_t n = a.hdr->visible;
+    const uint32_t *pay = a.hdr->sorted_buf ? a.pay[1] : a.pay[0];
+    uint64_t beg, end;
+    bin_range(a.ctas, n, &beg, &end);
+    unsigned long long sum = 0;
+    for (uint64_t k = beg + 4 * threadIdx.x; k < end; k += 4 * blockDim.x) {
+        uint32_t v[4];
+        if (k + 4 <= end) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(pay + k);
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = k + u < end ? pay[k + u] : 0x000000FFu;   // x0 > x1: empty
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const ushort4 t = unpack_tile_box(v[u]);
+            if (t.x <= t.z) sum += cells_of(t, kSuperShift);
+        }
+    }
+    unsigned long long tot;
+    block_exclusive_scan64<256>(sum, ws, &tot);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
+}
+
 __global__ void __launch_bounds__(256) k_bin_reduce(BinArgs a) {
     __shared__ unsigned long long ws[9];
     const uint32_t n = a.hdr->visible;
@@ -134,6 +169,7 @@ __global__ void __launch_bounds__(1024) k_bin_scan(BinArgs a) {
 // thread per round.  A thread finds its cell's warp from the warp totals and
 // its particle by binary search over the segment's first cells, so the work
 // is balanced whatever the particles' sizes.
+template <bool PAY>
 __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
     constexpr int kRounds = kBinStep / 256;
     __shared__ uint32_t s_lp[kBinStep];       // large particles, per warp segment of 256, in list order
@@ -143,6 +179,7 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
     __shared__ uint32_t s_wtot[3][8];         // per warp: cells, large particles, large cells
     const uint32_t n = a.hdr->visible;
     const uint32_t *list = a.hdr->sorted_buf ? a.list[1] : a.list[0];
+    const uint32_t *pay = a.hdr->sorted_buf ? a.pay[1] : a.pay[0];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t beg, end;
     bin_range(a.ctas, n, &beg, &end);
@@ -163,7 +200,7 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
             tb[q] = make_ushort4(1, 1, 0, 0);
             if (j < m) {
                 p[q] = list[step + j];
-                tb[q] = a.sbox[step + j];
+                tb[q] = PAY ? unpack_tile_box(pay[step + j]) : a.sbox[step + j];
                 if (tb[q].x <= tb[q].z) nt[q] = cells_of(tb[q], kSuperShift);
             }
             const bool big = nt[q] > a.large_tiles;
@@ -495,6 +532,7 @@ __global__ void __launch_bounds__(256) k_fine_emit(FineArgs a) {
     __shared__ uint32_t s_run[64];                  // entries placed so far per fine tile
     __shared__ uint32_t s_lb[65];                   // start of each fine tile's run in s_buf
     __shared__ unsigned long long s_gbase[64];      // list position of each fine tile's run
+    __shared__ uint8_t s_map[8][32];                // per warp: lane of each dealt entry, in lane order
     const uint32_t u = blockIdx.x;
     const uint32_t n_units = a.hdr->n_units;
     if (u >= n_units) return;
@@ -571,22 +609,51 @@ __global__ void __launch_bounds__(256) k_fine_emit(FineArgs a) {
             s_run[t] = run;
         }
         __syncthreads();
-        // (entry, fine tile) pairs of the warp, entry by entry, dealt over the lanes.  The
-        // entries with pairs are the warp's first lanes and begin at distinct pair indices,
-        // so a pair's entry is (entries begun before the round) + (entries begun in the round
-        // up to the pair) - 1, from one OR-reduction and one ballot per round.
+        // A pair's place in fine tile (r, c) is the warp's first place there plus the
+        // earlier lanes meeting (r, c): popc(row r & column c & lanes before).
         const uint32_t w = f.c1 - f.c0 + 1, h = f.r1 - f.r0 + 1;
-        const uint32_t npair = f.c0 <= f.c1 && f.r0 <= f.r1 ? w * h : 0u;
+        const uint32_t all_pairs = f.c0 <= f.c1 && f.r0 <= f.r1 ? w * h : 0u;
+        // An entry meeting at most 2 x 2 fine tiles (most of them) places its
+        // own pairs; the larger ones are dealt over the lanes below.
+        const bool own = all_pairs && w <= 2 && h <= 2;
+        if (own) {
+            const uint32_t lt = lanemask_lt();
+            for (uint32_t dr = 0; dr < h; ++dr)
+                for (uint32_t dc = 0; dc < w; ++dc) {
+                    const uint32_t r = (uint32_t)f.r0 + dr, c = (uint32_t)f.c0 + dc, t = r * kSuperSide + c;
+                    const uint32_t kk = s_pos[warp][t] + __popc(s_b[warp][r] & s_b[warp][kSuperSide + c] & lt);
+                    if (staged) {
+                        const uint32_t qq = s_lb[t] + kk;
+                        if (qq < (uint32_t)kFineBuf) s_buf[qq] = p;
+                    } else {
+                        const unsigned long long pos = s_gbase[t] + kk;
+                        if (pos < a.cap) a.list[pos] = p;
+                    }
+                }
+        }
+        // The other entries' (entry, fine tile) pairs, entry by entry, dealt over the lanes.
+        // Dealt entries begin at distinct pair indices, so a pair's entry is the m-th dealt
+        // entry, m = (dealt entries begun before the round) + (begun in the round up to the
+        // pair) - 1, from one OR-reduction and one ballot per round.
+        const uint32_t npair = own ? 0u : all_pairs;
         const uint32_t pinc = warp_inclusive_scan(npair);
         const uint32_t K = __shfl_sync(0xFFFFFFFFu, pinc, 31);
         const uint32_t start = pinc - npair;
         const uint32_t info = (uint32_t)f.c0 | ((uint32_t)f.r0 << 3) | (w << 6) | ((w ? 65536u / w + 1u : 0u) << 10);
         const uint32_t le = lanemask_lt() | (1u << lane);
+        if (K) {
+            // lane of the m-th dealt entry (dealt entries in lane order)
+            const uint32_t dealt = __ballot_sync(0xFFFFFFFFu, npair != 0u);
+            if (npair) s_map[warp][__popc(dealt & lanemask_lt())] = (uint8_t)lane;
+            __syncwarp();
+        }
         for (uint32_t q0 = 0; q0 < K; q0 += 32) {
             const bool begins = npair && start >= q0 && start < q0 + 32;
             const uint32_t H = __reduce_or_sync(0xFFFFFFFFu, begins ? 1u << (start - q0) : 0u);
             const uint32_t before = __popc(__ballot_sync(0xFFFFFFFFu, npair && start < q0));
-            const uint32_t o = min(before + __popc(H & le), 32u) - 1u;   // no entry begun: lane 31 (unused)
+            // rank of the pair's entry among the dealt ones (none begun yet: unused, any lane)
+            const uint32_t m = (before + __popc(H & le) - 1u) & 31u;
+            const uint32_t o = s_map[warp][m];
             const uint32_t ostart = __shfl_sync(0xFFFFFFFFu, start, o);
             const uint32_t oinfo = __shfl_sync(0xFFFFFFFFu, info, o);
             const uint32_t pp = __shfl_sync(0xFFFFFFFFu, p, o);
@@ -643,6 +710,8 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     a.hdr = hdr;
     a.list[0] = at<uint32_t>(ws, L.off_sv[0]);
     a.list[1] = at<uint32_t>(ws, L.off_sv[1]);
+    a.pay[0] = at<uint32_t>(ws, L.off_pay[0]);
+    a.pay[1] = at<uint32_t>(ws, L.off_pay[1]);
     a.box = at<ushort4>(ws, L.off_box);
     a.sbox = at<ushort4>(ws, L.off_sbox);
     a.tshift = tshift;
@@ -653,9 +722,13 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     a.cap = L.cap;
     a.nsx = (int)L.nsx;
     a.large_tiles = large_tiles;
-    k_bin_reduce<<<a.ctas, 256, 0, st>>>(a);
+    // the depth sort carried each particle's tile box when the tile counts fit its payload
+    const bool pay = tile_payload(L);
+    if (pay) k_bin_reduce_pay<<<a.ctas, 256, 0, st>>>(a);
+    else k_bin_reduce<<<a.ctas, 256, 0, st>>>(a);
     k_bin_scan<<<1, 1024, 0, st>>>(a);
-    k_bin_emit<<<a.ctas, 256, 0, st>>>(a);
+    if (pay) k_bin_emit<true><<<a.ctas, 256, 0, st>>>(a);
+    else k_bin_emit<false><<<a.ctas, 256, 0, st>>>(a);
     count_launches(3);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -32,6 +32,7 @@ struct Layout {
     uint32_t hist_ctas;      // max(sort_ctas, ent_ctas): rows of the histogram table
     uint32_t pad0;
     uint64_t off_geo, off_col, off_key, off_box, off_sbox;   // geo: {sx, sy, r2, -log2(e)/sigma_pix^2}; col: {Er, Eg, Eb, A}
+    uint64_t off_pay[2];     // tile-box payload of the depth sort (ping-pong), inside the sbox section
     uint64_t off_sk[2], off_sv[2];
     uint64_t off_part;
     uint64_t off_hist, off_htot;
@@ -137,6 +138,13 @@ struct RadixPass {
     uint32_t hist_stride;
     uint32_t *htot;            // [256]
     Header *hdr;
+    // Optional payload carried with each item (nullptr pay_out: none).  The
+    // first pass over particles makes it from the particle's pixel box
+    // (box_in, index order): its box in tiles, 8 bits per edge.
+    const ushort4 *box_in;
+    const uint32_t *pay_in;
+    uint32_t *pay_out;
+    int tshift;                // log2(tile side), for box_in
 };
 
 // Emission of (super-tile, particle) entries in render order.
@@ -152,6 +160,7 @@ struct BinArgs {
     const uint32_t *list[2];   // ordered visible list candidates (sorted_buf selects)
     const ushort4 *box;
     ushort4 *sbox;             // tile-level box per ordered position (written by the reduce, read by the emission)
+    const uint32_t *pay[2];    // or: the packed tile box carried through the depth sort (sorted_buf selects)
     int tshift;                // log2(tile side)
     uint64_t *part;            // per-CTA partial sums
     uint32_t ctas;
@@ -221,6 +230,24 @@ void count_launches(uint64_t k);
 cudaError_t launch_init_header(void *ws, const Layout &L, int n_species, int mode, cudaStream_t st);
 cudaError_t launch_transform(const TransformArgs &a, void *ws, const Layout &L, cudaStream_t st);
 cudaError_t launch_colorize(const ColorizeArgs &a, void *ws, const Layout &L, cudaStream_t st);
+// L2 cache size of the current device (bytes).
+uint64_t device_l2_bytes();
+
+// Whether the depth sort carries each visible particle's tile box for the
+// binning (a 32-bit payload, 8 bits per edge, so both tile counts must be at
+// most 256).  It replaces binning's one random gather (the box of each
+// particle in render order) by sequential reads, at the price of a third
+// array in every sort pass; that pays only when the boxes (8 B per particle)
+// do not stay in L2.
+// The environment variable SPLOTCH_TILE_PAYLOAD=1 (or 0) forces the choice
+// where the tile counts allow it (both paths give the same lists; tests use
+// it to cover both at small sizes).
+int tile_payload_override();   // -1: automatic, 0 or 1: forced
+inline bool tile_payload(const Layout &L) {
+    if (!(L.ntx <= 256 && L.nty <= 256)) return false;
+    const int o = tile_payload_override();
+    return o >= 0 ? o == 1 : L.n * 8 > device_l2_bytes();
+}
 cudaError_t launch_sort(void *ws, const Layout &L, int mode, cudaStream_t st);
 cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st);
 cudaError_t launch_sort_finish(Header *hdr, cudaStream_t st);   // absorptive ordering of a depth sort

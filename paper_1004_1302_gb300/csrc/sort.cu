@@ -116,9 +116,18 @@ constexpr int kDsThreads = 512;
 constexpr int kDsWarps = kDsThreads / 32;
 constexpr int kDsItems = kSortTile / kDsThreads;
 
+// The packed tile box of a particle (8 bits per edge: x0, y0, x1, y1 in
+// tiles) from its pixel box.
+__device__ __forceinline__ uint32_t pack_tile_box(const ushort4 b, int tshift) {
+    return (uint32_t)(b.x >> tshift) | ((uint32_t)(b.y >> tshift) << 8) | ((uint32_t)(b.z >> tshift) << 16) |
+           ((uint32_t)(b.w >> tshift) << 24);
+}
+
+template <bool PAY>
 __global__ void __launch_bounds__(kDsThreads) k_radix_downsweep(RadixPass P) {
     __shared__ uint32_t skey[kSortTile];
     __shared__ uint32_t sval[kSortTile];
+    __shared__ uint32_t spay[PAY ? kSortTile : 1];
     __shared__ uint16_t wcnt[kDsWarps][kRadix];   // per-warp digit counters (digit-contiguous: no bank conflicts)
     __shared__ uint32_t base[kRadix];
     __shared__ uint32_t lstart[kRadix + 1];
@@ -143,12 +152,18 @@ __global__ void __launch_bounds__(kDsThreads) k_radix_downsweep(RadixPass P) {
             reinterpret_cast<uint32_t *>(&wcnt[0][0])[q] = 0;
         __syncthreads();
         uint32_t key[kDsItems], val[kDsItems], dr[kDsItems];   // dr = rank << 9 | digit
+        uint32_t pay[PAY ? kDsItems : 1];
         const uint64_t wbase = tile + (uint64_t)warp * (kDsItems * 32);
 #pragma unroll
         for (int r = 0; r < kDsItems; ++r) {
             const uint64_t i = wbase + r * 32 + lane;
             key[r] = i < end ? P.key_in[i] : kInvalidKey;
             val[r] = i < end ? (P.val_in ? P.val_in[i] : (uint32_t)i) : 0u;
+            if (PAY) {
+                // the first pass makes the payload from the pixel box, only for the items it keeps
+                if (P.box_in) pay[r] = i < end && key[r] != kInvalidKey ? pack_tile_box(P.box_in[i], P.tshift) : 0u;
+                else pay[r] = i < end ? P.pay_in[i] : 0u;
+            }
         }
 #pragma unroll
         for (int r = 0; r < kDsItems; ++r) {
@@ -193,6 +208,7 @@ __global__ void __launch_bounds__(kDsThreads) k_radix_downsweep(RadixPass P) {
                 const uint32_t pos = wcnt[warp][d] + (dr[r] >> 9);
                 skey[pos] = key[r];
                 sval[pos] = val[r];
+                if (PAY) spay[pos] = pay[r];
             }
         }
         __syncthreads();
@@ -204,6 +220,7 @@ __global__ void __launch_bounds__(kDsThreads) k_radix_downsweep(RadixPass P) {
             if (SPL_CHECK(P.hdr, pos < n)) {
                 P.key_out[pos] = k;
                 P.val_out[pos] = sval[j];
+                if (PAY) P.pay_out[pos] = spay[j];
             }
         }
         __syncthreads();
@@ -215,7 +232,8 @@ __global__ void __launch_bounds__(kDsThreads) k_radix_downsweep(RadixPass P) {
 cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st) {
     k_radix_upsweep<<<p.ctas, kSortThreads, 0, st>>>(p);
     k_radix_scan<<<kRadix, 1024, 0, st>>>(p);
-    k_radix_downsweep<<<p.ctas, kDsThreads, 0, st>>>(p);
+    if (p.pay_out) k_radix_downsweep<true><<<p.ctas, kDsThreads, 0, st>>>(p);
+    else k_radix_downsweep<false><<<p.ctas, kDsThreads, 0, st>>>(p);
     count_launches(3);
     return cudaGetLastError();
 }
@@ -260,6 +278,14 @@ cudaError_t launch_sort(void *ws, const Layout &L, int mode, cudaStream_t st) {
     p.mask = absorptive ? 0xFFu : 0u;
     p.depth_pass = absorptive ? 0 : -1;
     p.skip_invalid = 1;
+    // the tile box of each visible particle travels with it, so binning reads
+    // it in render order instead of gathering it by index
+    const bool pay = tile_payload(L);
+    if (pay) {
+        p.box_in = at<ushort4>(ws, L.off_box);
+        p.pay_out = at<uint32_t>(ws, L.off_pay[0]);
+        p.tshift = L.tile == 8 ? 3 : (L.tile == 16 ? 4 : 5);
+    }
     cudaError_t e = L.n ? launch_radix_pass(p, st) : cudaSuccess;
     if (e != cudaSuccess) return e;
     if (absorptive) {
@@ -274,6 +300,11 @@ cudaError_t launch_sort(void *ws, const Layout &L, int mode, cudaStream_t st) {
             q.mask = 0xFFu;
             q.depth_pass = pass;
             q.skip_invalid = 0;
+            if (pay) {
+                q.box_in = nullptr;
+                q.pay_in = at<uint32_t>(ws, L.off_pay[(pass - 1) & 1]);
+                q.pay_out = at<uint32_t>(ws, L.off_pay[pass & 1]);
+            }
             e = launch_radix_pass(q, st);
             if (e != cudaSuccess) return e;
         }

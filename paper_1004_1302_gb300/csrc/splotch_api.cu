@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -16,6 +17,29 @@ static std::atomic<uint64_t> g_launches{0};
 void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 static uint64_t align256(uint64_t v) { return (v + 255u) & ~uint64_t(255u); }
+
+int tile_payload_override() {
+    static const int v = [] {
+        const char *e = std::getenv("SPLOTCH_TILE_PAYLOAD");
+        if (!e || !*e) return -1;
+        return e[0] == '1' ? 1 : (e[0] == '0' ? 0 : -1);
+    }();
+    return v;
+}
+
+uint64_t device_l2_bytes() {
+    static std::atomic<uint64_t> cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    uint64_t v = cached[dev].load(std::memory_order_relaxed);
+    if (!v) {
+        int b = 0;
+        cudaDeviceGetAttribute(&b, cudaDevAttrL2CacheSize, dev);
+        v = b > 0 ? (uint64_t)b : 1;
+        cached[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
 
 static uint32_t balanced_ctas(uint64_t items) {
     uint64_t tiles = (items + kSortTile - 1) / kSortTile;
@@ -50,7 +74,9 @@ int compute_layout(uint64_t n, int width, int height, int tile, uint64_t cap, La
     L.off_col = take(n * 16);
     L.off_key = take(n * 4);
     L.off_box = take(n * 8);
-    L.off_sbox = take(n * 8);
+    L.off_sbox = take(n * 8 + 256);
+    L.off_pay[0] = L.off_sbox;
+    L.off_pay[1] = L.off_sbox + align256(n * 4);
     for (int b = 0; b < 2; ++b) {
         L.off_sk[b] = take(n * 4);
         L.off_sv[b] = take(n * 4);

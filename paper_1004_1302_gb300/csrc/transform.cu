@@ -86,34 +86,29 @@ __device__ __forceinline__ Footprint footprint(const TransformArgs &a, float x, 
     return f;
 }
 
-template <int kVec>
+// A block takes kIlp x blockDim consecutive particles, thread t the particles
+// t, t + blockDim, ...: every load and store instruction of a warp covers
+// consecutive particles (coalesced), and the kIlp loads of each array are in
+// flight together.
+template <int kIlp>
 __global__ void __launch_bounds__(256) k_transform(TransformArgs a, float4 *geo, uint32_t *key, ushort4 *box,
-                                                   Header *hdr) {
+                                                     Header *hdr) {
     uint32_t nvis = 0, kmin = kInvalidKey, kmax = 0;
-    const uint64_t nvec = (a.n + kVec - 1) / kVec;
-    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nvec;
-         t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t i0 = t * kVec;
-        float xs[kVec], ys[kVec], zs[kVec], hs[kVec];
-        if (kVec == 4 && i0 + 4 <= a.n) {
-            float4 vx = __ldg(reinterpret_cast<const float4 *>(a.x) + t);
-            float4 vy = __ldg(reinterpret_cast<const float4 *>(a.y) + t);
-            float4 vz = __ldg(reinterpret_cast<const float4 *>(a.z) + t);
-            float4 vh = __ldg(reinterpret_cast<const float4 *>(a.h) + t);
-            xs[0] = vx.x; xs[1 % kVec] = vx.y; xs[2 % kVec] = vx.z; xs[3 % kVec] = vx.w;
-            ys[0] = vy.x; ys[1 % kVec] = vy.y; ys[2 % kVec] = vy.z; ys[3 % kVec] = vy.w;
-            zs[0] = vz.x; zs[1 % kVec] = vz.y; zs[2 % kVec] = vz.z; zs[3 % kVec] = vz.w;
-            hs[0] = vh.x; hs[1 % kVec] = vh.y; hs[2 % kVec] = vh.z; hs[3 % kVec] = vh.w;
-        } else {
+    const uint64_t chunk = (uint64_t)kIlp * blockDim.x;
+    for (uint64_t b = blockIdx.x * chunk; b < a.n; b += (uint64_t)gridDim.x * chunk) {
+        float xs[kIlp], ys[kIlp], zs[kIlp], hs[kIlp];
 #pragma unroll
-            for (int k = 0; k < kVec; ++k) {
-                uint64_t i = i0 + k < a.n ? i0 + k : a.n - 1;
-                xs[k] = __ldg(a.x + i); ys[k] = __ldg(a.y + i); zs[k] = __ldg(a.z + i); hs[k] = __ldg(a.h + i);
-            }
+        for (int k = 0; k < kIlp; ++k) {
+            const uint64_t i = b + threadIdx.x + (uint64_t)k * blockDim.x;
+            const uint64_t j = i < a.n ? i : a.n - 1;
+            xs[k] = __ldg(a.x + j);
+            ys[k] = __ldg(a.y + j);
+            zs[k] = __ldg(a.z + j);
+            hs[k] = __ldg(a.h + j);
         }
 #pragma unroll
-        for (int k = 0; k < kVec; ++k) {
-            const uint64_t i = i0 + k;
+        for (int k = 0; k < kIlp; ++k) {
+            const uint64_t i = b + threadIdx.x + (uint64_t)k * blockDim.x;
             if (i >= a.n) break;
             Footprint f = footprint(a, xs[k], ys[k], zs[k], hs[k]);
             geo[i] = f.geo;
@@ -282,21 +277,14 @@ cudaError_t launch_init_header(void *ws, const Layout &L, int n_species, int mod
 
 cudaError_t launch_transform(const TransformArgs &a, void *ws, const Layout &L, cudaStream_t st) {
     if (a.n == 0) return cudaGetLastError();
-    const bool aligned = ((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.y) |
-                           reinterpret_cast<uintptr_t>(a.z) | reinterpret_cast<uintptr_t>(a.h)) & 15u) == 0;
     const int sms = sm_count();
     float4 *geo = at<float4>(ws, L.off_geo);
     uint32_t *key = at<uint32_t>(ws, L.off_key);
     ushort4 *box = at<ushort4>(ws, L.off_box);
-    if (aligned) {
-        uint64_t blocks = (a.n + 4 * 256 - 1) / (4 * 256);
-        int grid = (int)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);
-        k_transform<4><<<grid, 256, 0, st>>>(a, geo, key, box, header(ws));
-    } else {
-        uint64_t blocks = (a.n + 255) / 256;
-        int grid = (int)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);
-        k_transform<1><<<grid, 256, 0, st>>>(a, geo, key, box, header(ws));
-    }
+    constexpr int kIlp = 4;
+    const uint64_t blocks = (a.n + kIlp * 256 - 1) / (kIlp * 256);
+    const int grid = (int)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);
+    k_transform<kIlp><<<grid, 256, 0, st>>>(a, geo, key, box, header(ws));
     count_launches(1);
     return cudaGetLastError();
 }

@@ -55,9 +55,9 @@ print("RESULT", __import__("json").dumps(out))
 '''
 
 
-def _run(tmp_path, checked: bool):
+def _run(tmp_path, checked: bool, payload: str):
     npz = str(tmp_path / ("checked.npz" if checked else "release.npz"))
-    env = dict(os.environ, SPLOTCH_CHECKED="1" if checked else "0")
+    env = dict(os.environ, SPLOTCH_CHECKED="1" if checked else "0", SPLOTCH_TILE_PAYLOAD=payload)
     r = subprocess.run([sys.executable, "-c", CASES.format(root=ROOT, npz=npz)], capture_output=True, text=True,
                        env=env, cwd=ROOT, timeout=900)
     assert r.returncode == 0, r.stderr[-3000:]
@@ -65,12 +65,13 @@ def _run(tmp_path, checked: bool):
     return json.loads(line[len("RESULT "):]), np.load(npz)
 
 
-def test_checked_build_passes_every_check_and_matches_release(tmp_path):
+@pytest.mark.parametrize("payload", ["0", "1"])   # tile boxes gathered by binning, or carried by the sort
+def test_checked_build_passes_every_check_and_matches_release(tmp_path, payload):
     from paper_1004_1302_gb300 import splotch as S
     S.build()
     S.build(checked=True)
-    res_c, img_c = _run(tmp_path, True)
-    res_r, img_r = _run(tmp_path, False)
+    res_c, img_c = _run(tmp_path, True, payload)
+    res_r, img_r = _run(tmp_path, False, payload)
     assert res_c["overflow_first"] == [S.ERR_WORKSPACE, 0]        # overflow reported, no index out of range
     for name, (status, line) in res_c.items():
         if name.endswith("_first"):
