@@ -532,7 +532,6 @@ __global__ void __launch_bounds__(256) k_fine_emit(FineArgs a) {
     __shared__ uint32_t s_run[64];                  // entries placed so far per fine tile
     __shared__ uint32_t s_lb[65];                   // start of each fine tile's run in s_buf
     __shared__ unsigned long long s_gbase[64];      // list position of each fine tile's run
-    __shared__ uint8_t s_map[8][32];                // per warp: lane of each dealt entry, in lane order
     const uint32_t u = blockIdx.x;
     const uint32_t n_units = a.hdr->n_units;
     if (u >= n_units) return;
@@ -609,51 +608,22 @@ __global__ void __launch_bounds__(256) k_fine_emit(FineArgs a) {
             s_run[t] = run;
         }
         __syncthreads();
-        // A pair's place in fine tile (r, c) is the warp's first place there plus the
-        // earlier lanes meeting (r, c): popc(row r & column c & lanes before).
+        // (entry, fine tile) pairs of the warp, entry by entry, dealt over the lanes.  The
+        // entries with pairs are the warp's first lanes and begin at distinct pair indices,
+        // so a pair's entry is (entries begun before the round) + (entries begun in the round
+        // up to the pair) - 1, from one OR-reduction and one ballot per round.
         const uint32_t w = f.c1 - f.c0 + 1, h = f.r1 - f.r0 + 1;
-        const uint32_t all_pairs = f.c0 <= f.c1 && f.r0 <= f.r1 ? w * h : 0u;
-        // An entry meeting at most 2 x 2 fine tiles (most of them) places its
-        // own pairs; the larger ones are dealt over the lanes below.
-        const bool own = all_pairs && w <= 2 && h <= 2;
-        if (own) {
-            const uint32_t lt = lanemask_lt();
-            for (uint32_t dr = 0; dr < h; ++dr)
-                for (uint32_t dc = 0; dc < w; ++dc) {
-                    const uint32_t r = (uint32_t)f.r0 + dr, c = (uint32_t)f.c0 + dc, t = r * kSuperSide + c;
-                    const uint32_t kk = s_pos[warp][t] + __popc(s_b[warp][r] & s_b[warp][kSuperSide + c] & lt);
-                    if (staged) {
-                        const uint32_t qq = s_lb[t] + kk;
-                        if (qq < (uint32_t)kFineBuf) s_buf[qq] = p;
-                    } else {
-                        const unsigned long long pos = s_gbase[t] + kk;
-                        if (pos < a.cap) a.list[pos] = p;
-                    }
-                }
-        }
-        // The other entries' (entry, fine tile) pairs, entry by entry, dealt over the lanes.
-        // Dealt entries begin at distinct pair indices, so a pair's entry is the m-th dealt
-        // entry, m = (dealt entries begun before the round) + (begun in the round up to the
-        // pair) - 1, from one OR-reduction and one ballot per round.
-        const uint32_t npair = own ? 0u : all_pairs;
+        const uint32_t npair = f.c0 <= f.c1 && f.r0 <= f.r1 ? w * h : 0u;
         const uint32_t pinc = warp_inclusive_scan(npair);
         const uint32_t K = __shfl_sync(0xFFFFFFFFu, pinc, 31);
         const uint32_t start = pinc - npair;
         const uint32_t info = (uint32_t)f.c0 | ((uint32_t)f.r0 << 3) | (w << 6) | ((w ? 65536u / w + 1u : 0u) << 10);
         const uint32_t le = lanemask_lt() | (1u << lane);
-        if (K) {
-            // lane of the m-th dealt entry (dealt entries in lane order)
-            const uint32_t dealt = __ballot_sync(0xFFFFFFFFu, npair != 0u);
-            if (npair) s_map[warp][__popc(dealt & lanemask_lt())] = (uint8_t)lane;
-            __syncwarp();
-        }
         for (uint32_t q0 = 0; q0 < K; q0 += 32) {
             const bool begins = npair && start >= q0 && start < q0 + 32;
             const uint32_t H = __reduce_or_sync(0xFFFFFFFFu, begins ? 1u << (start - q0) : 0u);
             const uint32_t before = __popc(__ballot_sync(0xFFFFFFFFu, npair && start < q0));
-            // rank of the pair's entry among the dealt ones (none begun yet: unused, any lane)
-            const uint32_t m = (before + __popc(H & le) - 1u) & 31u;
-            const uint32_t o = s_map[warp][m];
+            const uint32_t o = min(before + __popc(H & le), 32u) - 1u;   // no entry begun: lane 31 (unused)
             const uint32_t ostart = __shfl_sync(0xFFFFFFFFu, start, o);
             const uint32_t oinfo = __shfl_sync(0xFFFFFFFFu, info, o);
             const uint32_t pp = __shfl_sync(0xFFFFFFFFu, p, o);

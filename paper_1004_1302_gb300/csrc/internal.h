@@ -13,10 +13,9 @@ namespace spl {
 constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
 constexpr uint32_t kMagic = 0x5350'4C54u;  // "SPLT"
 
-// Radix sort geometry: 256 threads x 16 items = one 4096-item tile per step.
+// Radix sort geometry: items are ranked in tiles of kSortTile.
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortTile = 4096;
 constexpr int kRadix = 256;
 constexpr int kMaxSortCtas = 2048;
 
