@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--staging", type=int, default=0, choices=[0, 1],
+                    help="tile renderer staging of the headline frame: 0 register loads, 1 TMA gather4 copies")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the emission, e2e, CPU and form legs")
     ap.add_argument("--no-forms", action="store_true",
@@ -684,6 +686,18 @@ def figure_early_termination(args, dev, stream, dp, cam, pal, ref_img, cutoff=1e
             "status": int(fe.info().status)}
 
 
+def figure_tma_staging(args, dev, stream, dp, cam, pal, ref_img):
+    """The bench frame with the tile renderer's batches staged by TMA
+    tile::gather4 copies instead of per-thread register loads: render time
+    and the check that the image is the same bit for bit."""
+    from paper_1004_1302_gb300 import splotch as S
+    ft = S.Frame(dp, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev, staging=1)
+    img = ft.render().clone()
+    st = stage_times(ft, args.steps, 3, stream)
+    return {"render_ms": st["render"], "frame_ms": st["frame"], "identical_to_register_staging": bool((img == ref_img).all()),
+            "status": int(ft.info().status)}
+
+
 def figure_depth_slabs(args, dev, stream, dp, cam, pal, ref_img, keys, n_slabs=2):
     """The bench frame rendered as depth slabs of equal particle count, each
     a partial image (C, T), composed nearest first on the device: the one GPU
@@ -880,7 +894,7 @@ def main():
     ps, cam = synth.two_species()
     pal = synth.colormap()
     dp = S.upload(ps, dev, "f32")
-    fr = S.Frame(dp, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev)
+    fr = S.Frame(dp, cam, pal, S.ABSORPTIVE, tile=args.tile, batch=args.batch, device=dev, staging=args.staging)
     fr.render()                      # sizes the tile-entry capacity for this workload
     info = fr.info()
     if args.frames_only:
@@ -948,7 +962,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles": ps.n, "visible": int(info.visible),
                    "tile_entries": int(info.tile_entries), "fragments": F, "width": 1920, "height": 1080,
-                   "mode": "absorptive", "tile": args.tile, "batch": args.batch,
+                   "mode": "absorptive", "tile": args.tile, "batch": args.batch, "staging": args.staging,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (200 MB particle arrays, >1 GB workspace per frame)"},
         "frames_per_s": world * K / (total_ms * 1e-3),
@@ -1016,6 +1030,7 @@ def main():
         ref_img = fr.image.clone()
         out["early_termination"] = figure_early_termination(args, dev, stream, dp, cam, pal, ref_img)
         out["depth_slabs"] = figure_depth_slabs(args, dev, stream, dp, cam, pal, ref_img, keys)
+        out["tma_staging"] = figure_tma_staging(args, dev, stream, dp, cam, pal, ref_img)
         del ref_img
         # emission mode on the same particles
         fe = S.Frame(dp, cam, pal, S.EMISSION, tile=args.tile, batch=args.batch, device=dev)

@@ -136,6 +136,12 @@ typedef struct {
                                      pixel is at most T * M_c, Eq. 1 integrated over the remaining
                                      layers).  Never stops while a species with A = 0 emits.  Changes
                                      each channel by at most t_min_cutoff times its image maximum */
+    int32_t staging;              /* how the renderer stages a batch of a tile's list in shared memory:
+                                     0 (default): every thread loads its entries' records through registers;
+                                     1: cp.async.bulk.tensor tile::gather4 copies (TMA) land them directly,
+                                     for tiles of 16 and 32 px in the plain render (8-px tiles, partial
+                                     images and early termination load through registers).  The image is
+                                     the same bit for bit either way */
 } splotch_render_params;
 
 /* Result summary read back by splotch_frame_info (synchronises the stream). */

@@ -254,7 +254,7 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
 int super_passes(uint32_t nsuper);             // radix passes that group entries by super-tile
 uint64_t fine_list_offset(const Layout &L);    // workspace offset of the fine-tile lists
 cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float *image, float *trans, float cutoff,
-                          cudaStream_t st);
+                          int staging, cudaStream_t st);
 cudaError_t launch_compose(const float *cf, const float *tf, const float *cb, const float *tb, float *co, float *to,
                            uint64_t n, cudaStream_t st);
 cudaError_t launch_count_fragments(void *ws, const Layout &L, uint64_t *out, cudaStream_t st);

@@ -20,10 +20,62 @@
 // Packed f32x2 arithmetic does a pair of horizontally adjacent pixels in one
 // instruction.  Both layouts composite each pixel with the same operations in
 // the same order, so they give the same image bit for bit.
+#include <cuda.h>
+#include <cstring>
+#include <mutex>
+
 #include "internal.h"
 #include "device_util.cuh"
 
 namespace spl {
+
+// --- TMA staging of particle records ------------------------------------------
+// The records of a batch are named by the tile list, so they are gathered,
+// not copied as one range: a 2-D tensor map over each record array (rows =
+// particles, 4 floats per row) lets one cp.async.bulk.tensor tile::gather4
+// bring four rows (four particles) into shared memory, completing on an
+// mbarrier.  The copies need no registers and no per-thread load
+// instructions; threads only convert the landed records to operand pairs.
+struct TmaMaps {
+    CUtensorMap geo, col;   // rows of {sx, sy, r2, k} and {Er, Eg, Eb, A}
+};
+
+// Raw staging: kTmaStages stages (batches fetched kTmaStages - 1 ahead), per
+// stage and per group of four entries one 128-byte aligned block for each
+// record array (a gather4 writes 64 bytes).  Two, three and four stages gave
+// the same render time (4.00, 4.01, 3.97 ms on the bench frame), so two.
+constexpr int kTmaStages = 2;
+template <int B> struct TmaSmem {
+    __align__(128) float4 g[kTmaStages][B / 4][8];
+    __align__(128) float4 c[kTmaStages][B / 4][8];
+    __align__(8) unsigned long long bar[kTmaStages];
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, uint32_t r0, uint32_t r1, uint32_t r2,
+                                            uint32_t r3, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+        :: "r"(smem_addr(dst)), "l"(map), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Wait for phase `parity` of an mbarrier, at most `limit` polls; false if
+// the limit ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+constexpr uint32_t kTmaWaitPolls = 1u << 22;   // each try_wait blocks a while: far beyond any copy's time
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -292,8 +344,11 @@ constexpr int render_threads(int T) { return T >= 16 ? T * T / 4 : T * T / 2; }
 // a 2 x 2 square (two packed pixel pairs, one per row).  A step now composites
 // eight particles (one per group) on 128 pixels, and the column terms are
 // shared by the two rows.
-template <int T, int MODE, int B, bool SERIES, bool ET, bool PT>
-__device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile, RenderSmem<B> &sm) {
+// TMA: the batches are staged by tile::gather4 copies (maps, ts) instead of
+// per-thread loads through registers.
+template <int T, int MODE, int B, bool SERIES, bool ET, bool PT, bool TMA = false>
+__device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile, RenderSmem<B> &sm,
+                                             const TmaMaps *maps = nullptr, TmaSmem<B> *ts = nullptr) {
     constexpr int kThreads = T * T / 4;
     constexpr int WX = 16, WY = 8;
     constexpr int kWarpCols = T / WX;
@@ -326,28 +381,68 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
     const bool ok = a.hdr->status == SPLOTCH_OK;
     const uint32_t begin = ok ? a.toff[tile] : 0u, end = ok ? a.toff[tile + 1] : 0u;
 
-    float4 rg[kPer], rc[kPer];
-    auto load = [&](uint32_t base) {
+    float4 rg[TMA ? 1 : kPer], rc[TMA ? 1 : kPer];
+    // batch staging: `load` starts fetching the batch at `base`, `store` writes
+    // it to the operand buffer `buf` once it has arrived (`stage`: TMA stage)
+    auto load = [&](uint32_t base, int stage) {
         const uint32_t nb = min((uint32_t)B, end - base);
+        if constexpr (TMA) {
+            // warp 0: lane g gathers entries 4g .. 4g + 3 (rows past the batch read particle 0, unused)
+            if (threadIdx.x < 32) {
+                const uint32_t ng = (nb + 3) / 4;
+                if (threadIdx.x == 0) {
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                                 :: "r"(smem_addr(&ts->bar[stage])), "r"(ng * 128u) : "memory");
+                }
+                __syncwarp();
+                // the stage's previous records were read by generic loads before the barrier that
+                // precedes this call: order them before the copies that overwrite them
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                for (uint32_t g = threadIdx.x; g < ng; g += 32) {
+                    uint32_t r[4];
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const uint32_t j = threadIdx.x + q * kThreads;
-            if (j < nb && SPL_CHECK(a.hdr, base + j < a.hdr->layout.cap)) {
-                const uint32_t p = __ldg(&a.list[base + j]);
-                if (SPL_CHECK(a.hdr, p < a.hdr->layout.n)) {
-                    rg[q] = __ldg(&a.geo[p]);
-                    rc[q] = __ldg(&a.col[p]);
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t j = 4 * g + k;
+                        r[k] = 0;
+                        if (j < nb && SPL_CHECK(a.hdr, base + j < a.hdr->layout.cap)) {
+                            const uint32_t p = __ldg(&a.list[base + j]);
+                            if (SPL_CHECK(a.hdr, p < a.hdr->layout.n)) r[k] = p;
+                        }
+                    }
+                    tma_gather4(&ts->g[stage][g][0], &maps->geo, r[0], r[1], r[2], r[3], &ts->bar[stage]);
+                    tma_gather4(&ts->c[stage][g][0], &maps->col, r[0], r[1], r[2], r[3], &ts->bar[stage]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const uint32_t j = threadIdx.x + q * kThreads;
+                if (j < nb && SPL_CHECK(a.hdr, base + j < a.hdr->layout.cap)) {
+                    const uint32_t p = __ldg(&a.list[base + j]);
+                    if (SPL_CHECK(a.hdr, p < a.hdr->layout.n)) {
+                        rg[q] = __ldg(&a.geo[p]);
+                        rc[q] = __ldg(&a.col[p]);
+                    }
                 }
             }
         }
     };
-    auto store = [&](int buf, uint32_t base) {
+    // batch k sits in stage k % kTmaStages and is the (k / kTmaStages)-th use of that
+    // stage's barrier: phase parity (k / kTmaStages) & 1
+    uint32_t nstored = 0;
+    auto store = [&](int buf, uint32_t base, int stage) {
         const uint32_t nb = min((uint32_t)B, end - base);
+        if constexpr (TMA) {
+            if (!mbar_wait(&ts->bar[stage], (nstored / kTmaStages) & 1u, kTmaWaitPolls) && threadIdx.x == 0)
+                atomicExch(const_cast<int *>(&a.hdr->status), (int)SPLOTCH_ERR_TIMEOUT);
+            nstored += 1;
+        }
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const uint32_t j = threadIdx.x + q * kThreads;
             if (j < nb) {
-                const float4 g = rg[q], c = rc[q];
+                const float4 g = TMA ? ts->g[stage][j >> 2][j & 3] : rg[q];
+                const float4 c = TMA ? ts->c[stage][j >> 2][j & 3] : rc[q];
                 const uint32_t sl = (j >> 5) * 33 + 1 + (j & 31);
                 s0[buf][sl] = make_float4(-g.x, -g.x, -g.y, -g.y);
                 s1[buf][sl] = make_float4(g.w, g.w, -c.w, -c.w);
@@ -366,9 +461,21 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
         s2[nbuf][sl] = z;
         s3[nbuf][sl] = z;
     }
+    if constexpr (TMA) {
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < kTmaStages; ++k)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&ts->bar[k])) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
     if (begin < end) {
-        load(begin);
-        store(0, begin);
+        if constexpr (TMA) {
+            for (int k = 0; k < kTmaStages - 1 && begin + (uint32_t)k * B < end; ++k) load(begin + k * B, k);
+        } else {
+            load(begin, 0);
+        }
+        store(0, begin, 0);
     }
     int buf = 0;
     // one row (pixel pair) of the lane's square: weight, transfer and colour
@@ -406,10 +513,18 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
         row(__ffma2_rn(dyA, dyA, dx2), p1, p2, p3, crA, cgA, cbA, tA);
         row(__ffma2_rn(dyB, dyB, dx2), p1, p2, p3, crB, cgB, cbB, tB);
     };
-    for (uint32_t base = begin; base < end; base += B, buf ^= 1) {
+    int stage = 0;   // TMA stage of the batch being composited
+    for (uint32_t base = begin; base < end; base += B, buf ^= 1, stage = stage + 1 == kTmaStages ? 0 : stage + 1) {
         const uint32_t next = base + B;
-        if (next < end) load(next);
+        const int nstage = stage + 1 == kTmaStages ? 0 : stage + 1;
+        if (!TMA && next < end) load(next, 0);
         __syncthreads();
+        // after the barrier every thread has converted the current batch: the stage of the
+        // batch before it is free for the batch kTmaStages - 1 ahead
+        if (TMA) {
+            const uint32_t ahead = base + (uint32_t)(kTmaStages - 1) * B;
+            if (ahead < end) load(ahead, stage == 0 ? kTmaStages - 1 : stage - 1);
+        }
         const uint32_t nb = min((uint32_t)B, end - base);
         for (uint32_t c = 0; c < (ET && wdone ? 0u : nb); c += 32) {
             // each lane tests entry c + lane against the eight quadrants (4 columns x 2 rows)
@@ -470,11 +585,23 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
                 };
                 wdone = warp_converged(mx4(tA, tB), mx4(crA, crB), mx4(cgA, cgB), mx4(cbA, cbB), M, a.cutoff);
             }
-            if (__syncthreads_and(wdone)) break;
+            if (__syncthreads_and(wdone)) {
+                // the next batch's copies may be in flight: let them land before leaving
+                if (TMA) {
+                    // wait for every batch still in flight
+                    uint32_t k = nstored;
+                    int st = nstage;
+                    for (uint32_t b2 = next; b2 < end && b2 < base + (uint32_t)kTmaStages * B; b2 += B, ++k) {
+                        mbar_wait(&ts->bar[st], (k / kTmaStages) & 1u, kTmaWaitPolls);
+                        st = st + 1 == kTmaStages ? 0 : st + 1;
+                    }
+                }
+                break;
+            }
         } else {
             __syncthreads();
         }
-        if (next < end) store(buf ^ 1, next);
+        if (next < end) store(buf ^ 1, next, nstage);
     }
 
     // transmittance of a partial render (E = A: exp(-tau) before C = 1 - exp(-tau))
@@ -527,13 +654,21 @@ __device__ __forceinline__ void render_any(const RenderArgs &a, const int tile, 
 // per SM): 3.40 -> 3.36 ms against the 80 registers and small spills it
 // chose without the bound; capping at 72 (14 CTAs) or unrolling four steps
 // was slower (3.52 ms).
-template <int T, int MODE, int B, bool ET, bool PT>
-__global__ void __launch_bounds__(render_threads(T), 1) k_render(RenderArgs a) {
+// TMA: batches staged by tile::gather4 copies (tiles of 16 and 32, plain render).
+template <int T, int MODE, int B, bool ET, bool PT, bool TMA>
+__global__ void __launch_bounds__(render_threads(T), 1) k_render(RenderArgs a, const __grid_constant__ TmaMaps maps) {
     __shared__ __align__(16) RenderSmem<B> sm;
     const uint32_t tile = __ldg(&a.torder[blockIdx.x]);
     if (tile >= gridDim.x) return;   // a workspace that was never binned
-    if (MODE == SPLOTCH_ABSORPTIVE && a.hdr->series_only) render_any<T, MODE, B, true, ET, PT>(a, (int)tile, sm);
-    else render_any<T, MODE, B, false, ET, PT>(a, (int)tile, sm);
+    const bool series = MODE == SPLOTCH_ABSORPTIVE && a.hdr->series_only;
+    if constexpr (TMA) {
+        __shared__ TmaSmem<B> ts;
+        if (series) render_tile4<T, MODE, B, true, ET, PT, true>(a, (int)tile, sm, &maps, &ts);
+        else render_tile4<T, MODE, B, false, ET, PT, true>(a, (int)tile, sm, &maps, &ts);
+    } else {
+        if (series) render_any<T, MODE, B, true, ET, PT>(a, (int)tile, sm);
+        else render_any<T, MODE, B, false, ET, PT>(a, (int)tile, sm);
+    }
 }
 
 // Persistent render of the tiles of many frames: each CTA takes the next
@@ -568,31 +703,68 @@ __global__ void __launch_bounds__(render_threads(T)) k_render_batch(const __grid
     }
 }
 
-template <int T, int MODE, bool ET, bool PT>
-static void launch_tb(const RenderArgs &a, int ntiles, cudaStream_t st) {
+template <int T, int MODE, bool ET, bool PT, bool TMA>
+static void launch_tb(const RenderArgs &a, const TmaMaps &m, int ntiles, cudaStream_t st) {
     switch (a.batch) {
-    case 64: k_render<T, MODE, 64, ET, PT><<<ntiles, render_threads(T), 0, st>>>(a); break;
-    case 128: k_render<T, MODE, 128, ET, PT><<<ntiles, render_threads(T), 0, st>>>(a); break;
-    default: k_render<T, MODE, 256, ET, PT><<<ntiles, render_threads(T), 0, st>>>(a); break;
+    case 64: k_render<T, MODE, 64, ET, PT, TMA><<<ntiles, render_threads(T), 0, st>>>(a, m); break;
+    case 128: k_render<T, MODE, 128, ET, PT, TMA><<<ntiles, render_threads(T), 0, st>>>(a, m); break;
+    default: k_render<T, MODE, 256, ET, PT, TMA><<<ntiles, render_threads(T), 0, st>>>(a, m); break;
     }
 }
 
 template <int T, int MODE, bool ET>
-static void launch_tp(const RenderArgs &a, int ntiles, cudaStream_t st) {
-    if (a.trans) launch_tb<T, MODE, ET, true>(a, ntiles, st);
-    else launch_tb<T, MODE, ET, false>(a, ntiles, st);
+static void launch_tp(const RenderArgs &a, const TmaMaps &m, bool tma, int ntiles, cudaStream_t st) {
+    if (a.trans) {
+        launch_tb<T, MODE, ET, true, false>(a, m, ntiles, st);
+    } else if constexpr (T >= 16 && !ET) {
+        if (tma) launch_tb<T, MODE, ET, false, true>(a, m, ntiles, st);
+        else launch_tb<T, MODE, ET, false, false>(a, m, ntiles, st);
+    } else {
+        launch_tb<T, MODE, ET, false, false>(a, m, ntiles, st);
+    }
 }
 
 template <int T>
-static void launch_t(const RenderArgs &a, int ntiles, cudaStream_t st) {
+static void launch_t(const RenderArgs &a, const TmaMaps &m, bool tma, int ntiles, cudaStream_t st) {
     switch (a.mode) {
-    case SPLOTCH_EMISSION: launch_tp<T, SPLOTCH_EMISSION, false>(a, ntiles, st); break;
+    case SPLOTCH_EMISSION: launch_tp<T, SPLOTCH_EMISSION, false>(a, m, tma, ntiles, st); break;
     case SPLOTCH_ABSORPTIVE:
-        if (a.cutoff > 0.0f) launch_tp<T, SPLOTCH_ABSORPTIVE, true>(a, ntiles, st);
-        else launch_tp<T, SPLOTCH_ABSORPTIVE, false>(a, ntiles, st);
+        if (a.cutoff > 0.0f) launch_tp<T, SPLOTCH_ABSORPTIVE, true>(a, m, tma, ntiles, st);
+        else launch_tp<T, SPLOTCH_ABSORPTIVE, false>(a, m, tma, ntiles, st);
         break;
-    default: launch_tp<T, SPLOTCH_E_EQ_A, false>(a, ntiles, st); break;
+    default: launch_tp<T, SPLOTCH_E_EQ_A, false>(a, m, tma, ntiles, st); break;
     }
+}
+
+// cuTensorMapEncodeTiled, found through the runtime (no link against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// A tensor map over n records of 4 floats (16 B): rows of one particle, a box
+// of one row (the shape a tile::gather4 copy takes).
+static bool encode_records(CUtensorMap *m, const float4 *base, uint64_t n) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {4, n ? n : 1};
+    const cuuint64_t strides[1] = {16};
+    const cuuint32_t box[2] = {4, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float4 *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, float *image, float *trans,
@@ -617,12 +789,17 @@ RenderArgs make_render_args(void *ws, const Layout &L, int mode, int batch, floa
 }
 
 cudaError_t launch_render(void *ws, const Layout &L, int mode, int batch, float *image, float *trans, float cutoff,
-                          cudaStream_t st) {
+                          int staging, cudaStream_t st) {
     const RenderArgs a = make_render_args(ws, L, mode, batch, image, trans, cutoff);
+    TmaMaps m;
+    std::memset(&m, 0, sizeof(m));
+    const bool tma = staging == 1 && L.tile >= 16 && !trans && !(a.cutoff > 0.0f);
+    if (tma && (!encode_records(&m.geo, a.geo, L.n) || !encode_records(&m.col, a.col, L.n)))
+        return cudaErrorNotSupported;
     switch (L.tile) {
-    case 8: launch_t<8>(a, (int)L.ntiles, st); break;
-    case 32: launch_t<32>(a, (int)L.ntiles, st); break;
-    default: launch_t<16>(a, (int)L.ntiles, st); break;
+    case 8: launch_t<8>(a, m, false, (int)L.ntiles, st); break;
+    case 32: launch_t<32>(a, m, tma, (int)L.ntiles, st); break;
+    default: launch_t<16>(a, m, tma, (int)L.ntiles, st); break;
     }
     count_launches(1);
     return cudaGetLastError();

@@ -120,6 +120,7 @@ static int check_params(const splotch_render_params *pr) {
     if (!(pr->sigma_per_h > 0.0f) || !(pr->trunc_f > 0.0f) || pr->large_threshold_px < 0) return SPLOTCH_ERR_ARG;
     if (pr->slab != 0 && pr->slab != 1) return SPLOTCH_ERR_ARG;
     if (!(pr->t_min_cutoff >= 0.0f) || !(pr->t_min_cutoff < 1.0f)) return SPLOTCH_ERR_ARG;
+    if (pr->staging != 0 && pr->staging != 1) return SPLOTCH_ERR_ARG;
     return SPLOTCH_OK;
 }
 
@@ -322,7 +323,7 @@ int splotch_render_tiles(const splotch_render_params *params, const splotch_came
     if ((s = check_ws(workspace, workspace_bytes, L))) return s;
     if (!image) return SPLOTCH_ERR_ARG;
     return cuda_status(launch_render(workspace, L, params->mode, params->batch, image, nullptr,
-                                     params->t_min_cutoff, static_cast<cudaStream_t>(stream)));
+                                     params->t_min_cutoff, params->staging, static_cast<cudaStream_t>(stream)));
 }
 
 int splotch_render_partial(const splotch_render_params *params, const splotch_camera *cam, uint64_t n,
@@ -334,7 +335,7 @@ int splotch_render_partial(const splotch_render_params *params, const splotch_ca
     Layout L;
     frame_layout(params, cam, n, &L);
     return cuda_status(launch_render(workspace, L, params->mode, params->batch, color, trans, params->t_min_cutoff,
-                                     static_cast<cudaStream_t>(stream)));
+                                     params->staging, static_cast<cudaStream_t>(stream)));
 }
 
 int splotch_compose(const float *c_front, const float *t_front, const float *c_back, const float *t_back,

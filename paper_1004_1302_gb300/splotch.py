@@ -105,7 +105,7 @@ class RenderParams(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tile", ctypes.c_int32), ("sigma_per_h", ctypes.c_float),
                 ("trunc_f", ctypes.c_float), ("batch", ctypes.c_int32), ("large_threshold_px", ctypes.c_int32),
                 ("max_tile_entries", ctypes.c_uint64), ("slab", ctypes.c_int32), ("slab_key_lo", ctypes.c_uint32),
-                ("slab_key_hi", ctypes.c_uint32), ("t_min_cutoff", ctypes.c_float)]
+                ("slab_key_hi", ctypes.c_uint32), ("t_min_cutoff", ctypes.c_float), ("staging", ctypes.c_int32)]
 
 
 class BatchItem(ctypes.Structure):
@@ -421,8 +421,9 @@ def make_species(sp) -> SpeciesParams:
 
 def make_params(mode: int, tile: int = 16, batch: int = 64, sigma_per_h: float = 1.0, trunc_f: float = 2.0,
                 large_threshold_px: int = 0, max_tile_entries: int = 0, slab=None,
-                t_min_cutoff: float = 0.0) -> RenderParams:
-    """slab: None, or (key_lo, key_hi) to keep only depth keys in [key_lo, key_hi)."""
+                t_min_cutoff: float = 0.0, staging: int = 0) -> RenderParams:
+    """slab: None, or (key_lo, key_hi) to keep only depth keys in [key_lo, key_hi).
+    staging: 0 register loads, 1 TMA gather4 copies (see include/splotch.h)."""
     p = RenderParams()
     p.mode, p.tile, p.batch = int(mode), int(tile), int(batch)
     p.sigma_per_h, p.trunc_f = float(sigma_per_h), float(trunc_f)
@@ -431,6 +432,7 @@ def make_params(mode: int, tile: int = 16, batch: int = 64, sigma_per_h: float =
     if slab is not None:
         p.slab, p.slab_key_lo, p.slab_key_hi = 1, int(slab[0]), int(slab[1])
     p.t_min_cutoff = float(t_min_cutoff)
+    p.staging = int(staging)
     return p
 
 
@@ -514,7 +516,8 @@ class Frame:
 
     def __init__(self, dp: DeviceParticles, cam_spec, palette, mode: int, tile: int = 16, batch: int = 64,
                  sigma_per_h: float = 1.0, trunc_f: float = 2.0, large_threshold_px: int = 0,
-                 max_tile_entries: int | None = None, device="cuda", slab=None, t_min_cutoff: float = 0.0):
+                 max_tile_entries: int | None = None, device="cuda", slab=None, t_min_cutoff: float = 0.0,
+                 staging: int = 0):
         import torch
         self.torch = torch
         self.dp = dp
@@ -528,7 +531,7 @@ class Frame:
             ntiles = math.ceil(self.W / tile) * math.ceil(self.H / tile)
             max_tile_entries = max(4 * dp.n, 1024) + ntiles
         self.params = make_params(mode, tile, batch, sigma_per_h, trunc_f, large_threshold_px, max_tile_entries,
-                                  slab, t_min_cutoff)
+                                  slab, t_min_cutoff, staging)
         self.pstruct = dp.struct()
         self.trans = None
         self.species = [make_species(s) for s in dp.species]

@@ -84,6 +84,8 @@ def test_workspace_size_and_arguments(S):
     for bad in (dict(t_min_cutoff=-1e-6), dict(t_min_cutoff=1.0), dict(t_min_cutoff=float("nan"))):
         q = S.make_params(S.ABSORPTIVE, max_tile_entries=1024, **bad)
         assert lib.splotch_workspace_size(1000, ctypes.byref(cam), ctypes.byref(q), ctypes.byref(out)) == S.ERR_ARG
+    q = S.make_params(S.ABSORPTIVE, max_tile_entries=1024, staging=2)
+    assert lib.splotch_workspace_size(1000, ctypes.byref(cam), ctypes.byref(q), ctypes.byref(out)) == S.ERR_ARG
     q = S.make_params(S.ABSORPTIVE, max_tile_entries=1024, slab=(0, 10))
     assert lib.splotch_workspace_size(1000, ctypes.byref(cam), ctypes.byref(q), ctypes.byref(out)) == S.OK
     q.slab = 2

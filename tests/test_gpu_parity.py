@@ -92,6 +92,27 @@ def test_two_species_ragged(mode, tile):
     _compare_frame(g, o)
 
 
+@pytest.mark.parametrize("batch", [64, 256])
+@pytest.mark.parametrize("tile", [16, 32])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_tma_staging_gives_the_same_image(mode, tile, batch):
+    """Batches staged by TMA tile::gather4 copies composite the same records
+    in the same order as the register staging: the same image bit for bit,
+    hence the oracle's within the tolerance (ragged tiles, partial last
+    batches)."""
+    from paper_1004_1302_gb300 import splotch as S
+    ps, cam = small_two_species(60_000, 330, 190)
+    pal = synth.colormap()
+    dp = S.upload(ps, "cuda", "f32")
+    ref = S.Frame(dp, cam, pal, mode, tile=tile, batch=batch).render().clone()
+    fr = S.Frame(dp, cam, pal, mode, tile=tile, batch=batch, staging=1)
+    img = fr.render()
+    assert fr.info().status == S.OK
+    assert bool((img == ref).all())
+    o = oracle_render(ps, cam, pal, mode, tile=tile)
+    assert (image_error(img.cpu().numpy(), o.image) <= TOL).all()
+
+
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])
 def test_reduced_precision_intensity(dtype):
     ps, cam = small_two_species(80_000, 320, 180)
