@@ -190,8 +190,8 @@ int splotch_workspace_size(uint64_t n, const splotch_camera *cam, const splotch_
  *   X  = fmaf(z, r2, fmaf(y, r1, x * r0)) - (float)c_right      in float (basis rounded to float), Y likewise
  *   inv = 1 / (float)Z;  sx = W/2 + (s * X) * inv;  sy = H/2 - (s * Y) * inv    (s = (float)scale)
  *   sigma_pix = (s * (sigma_per_h * h)) * inv;  r = trunc_f * sigma_pix;  r2 = r * r
- *   box x0 = max(0, floor((sx - r) - 0.5)), x1 = min(W - 1, floor((sx + r) - 0.5) + 1), y likewise;
- *       culled when empty or not finite
+ *   box x0 = max(0, ceil(((sx - r) - 0.5) - 1/64)), x1 = min(W - 1, floor(((sx + r) - 0.5) + 1/64)),
+ *       y likewise; culled when empty (no pixel centre within reach) or not finite
  * Pixel (i, j) (centre (i + 0.5, j + 0.5), row 0 on top) receives the
  * particle iff fmaf(dy, dy, dx * dx) < r2 with dx = (i + 0.5f) - sx,
  * dy = (j + 0.5f) - sy; such a pixel always lies in the box.

@@ -108,11 +108,14 @@ int oracle_camera(ocam *c)
  *   inv  = 1 / (float)Z
  *   sx   = W/2 + (s * X) * inv,  sy = H/2 - (s * Y) * inv
  *   sigma_pix = (s * (sigma_per_h * h)) * inv, r = f * sigma_pix, r2 = r * r
- *   bbox: floor((sx - r) - 1/2) .. floor((sx + r) - 1/2) + 1, clipped to the image;
- *         culled when empty.  The floor on the low side and the +1 on the high
- *         side leave a margin of up to one pixel beyond the disc, enough to
- *         absorb single-precision rounding: every pixel that passes the C6 test
- *         lies inside the box.
+ *   bbox: ceil(((sx - r) - 1/2) - 1/64) .. floor(((sx + r) - 1/2) + 1/64),
+ *         clipped to the image; culled when empty (no pixel centre can pass
+ *         the cut).  Pixel i passes the C6 test only if its centre lies within
+ *         r of sx up to single-precision rounding: fl(dx*dx) <= the fused sum
+ *         and both squares are rounded once, so |(i + 1/2) - sx| < r (1 + 2^-22)
+ *         roughly; the 1/64 px guard covers that and the rounding of the box
+ *         arithmetic itself (a few ulp of values below 2^16), so every pixel
+ *         that passes the C6 test lies inside the box.
  * Outputs are per input index; bbox holds x0, y0, x1, y1.
  */
 void oracle_geometry(const ocam *c, size_t n, const float *x, const float *y, const float *z, const float *h,
@@ -144,8 +147,9 @@ void oracle_geometry(const ocam *c, size_t n, const float *x, const float *y, co
         float py = hh - (s * Y) * inv;
         float sg = (s * (sigma_per_h * h[i])) * inv;
         float r = trunc_f * sg;
-        float lx = floorf((px - r) - 0.5f), hx = floorf((px + r) - 0.5f) + 1.0f;
-        float ly = floorf((py - r) - 0.5f), hy = floorf((py + r) - 0.5f) + 1.0f;
+        const float G = 0.015625f; /* 1/64 px guard, see the comment above */
+        float lx = ceilf(((px - r) - 0.5f) - G), hx = floorf(((px + r) - 0.5f) + G);
+        float ly = ceilf(((py - r) - 0.5f) - G), hy = floorf(((py + r) - 0.5f) + G);
         float x0 = lx > 0.0f ? lx : 0.0f, x1 = hx < wmax ? hx : wmax;
         float y0 = ly > 0.0f ? ly : 0.0f, y1 = hy < hmax ? hy : hmax;
         if (!(lx <= hx) || !(ly <= hy) || !(x0 <= x1) || !(y0 <= y1))

@@ -116,8 +116,12 @@ constexpr int kDsThreads = 512;
 // Four CTAs per SM (32 registers, a few spilled): the ranking waits on
 // barriers, and more resident CTAs hide them better than the registers save
 // (depth sort 0.315 -> 0.306 ms and the grouping pass 8 us faster at 10M
-// particles than with 62 registers and 2 CTAs; 3 CTAs: 0.319 ms).
+// particles than with 62 registers and 2 CTAs; 3 CTAs: 0.319 ms).  The
+// variant carrying a payload keeps two CTAs (its third shared array and
+// registers; forced to four it spilled more and the 1.07e9-particle sort
+// took 43.6 instead of 35.0 ms).
 constexpr int kDsMinBlocks = 4;
+constexpr int kDsMinBlocksPay = 2;
 constexpr int kDsWarps = kDsThreads / 32;
 constexpr int kDsItems = kSortTile / kDsThreads;
 
@@ -129,7 +133,7 @@ __device__ __forceinline__ uint32_t pack_tile_box(const ushort4 b, int tshift) {
 }
 
 template <bool PAY>
-__global__ void __launch_bounds__(kDsThreads, kDsMinBlocks) k_radix_downsweep(RadixPass P) {
+__global__ void __launch_bounds__(kDsThreads, PAY ? kDsMinBlocksPay : kDsMinBlocks) k_radix_downsweep(RadixPass P) {
     __shared__ uint32_t skey[kSortTile];
     __shared__ uint32_t sval[kSortTile];
     __shared__ uint32_t spay[PAY ? kSortTile : 1];

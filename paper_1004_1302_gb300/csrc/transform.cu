@@ -73,10 +73,13 @@ __device__ __forceinline__ Footprint footprint(const TransformArgs &a, float x, 
     float py = __fsub_rn(a.half_h, __fmul_rn(__fmul_rn(a.s, Y), inv));
     float sg = __fmul_rn(__fmul_rn(a.s, __fmul_rn(a.sigma_per_h, h)), inv);
     float r = __fmul_rn(a.trunc_f, sg);
-    float lx = floorf(__fsub_rn(__fsub_rn(px, r), 0.5f));
-    float hx = __fadd_rn(floorf(__fsub_rn(__fadd_rn(px, r), 0.5f)), 1.0f);
-    float ly = floorf(__fsub_rn(__fsub_rn(py, r), 0.5f));
-    float hy = __fadd_rn(floorf(__fsub_rn(__fadd_rn(py, r), 0.5f)), 1.0f);
+    // pixel box: the centres within r of (px, py), widened by a 1/64 px guard
+    // that covers the rounding of the cut test and of these operations
+    constexpr float kGuard = 0.015625f;
+    float lx = ceilf(__fsub_rn(__fsub_rn(__fsub_rn(px, r), 0.5f), kGuard));
+    float hx = floorf(__fadd_rn(__fsub_rn(__fadd_rn(px, r), 0.5f), kGuard));
+    float ly = ceilf(__fsub_rn(__fsub_rn(__fsub_rn(py, r), 0.5f), kGuard));
+    float hy = floorf(__fadd_rn(__fsub_rn(__fadd_rn(py, r), 0.5f), kGuard));
     float x0 = lx > 0.0f ? lx : 0.0f, x1 = hx < a.w_max ? hx : a.w_max;
     float y0 = ly > 0.0f ? ly : 0.0f, y1 = hy < a.h_max ? hy : a.h_max;
     if (!(lx <= hx) || !(ly <= hy) || !(x0 <= x1) || !(y0 <= y1)) return f;

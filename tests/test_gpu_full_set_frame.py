@@ -47,7 +47,7 @@ def test_full_set_frame_matches_oracle_on_sampled_pixels(oracle_mod):
     fr = S.Frame(dp, cam, pal, S.ABSORPTIVE, tile=16, batch=128, max_tile_entries=int(2.2 * n))
     img = fr.render().cpu().numpy().astype(np.float64)
     info = fr.info()
-    assert info.status == 0 and info.visible > 0.9 * n
+    assert info.status == 0 and info.visible > 0.85 * n   # footprints reaching no pixel centre are culled
     rng = np.random.default_rng(17)
     key_idx = np.sort(rng.choice(n, 20000, replace=False))
     gpu_key, _ = fr.keys()

@@ -50,7 +50,8 @@ def test_plummer_mixture_100k_emission_full_size():
     g = gpu_render(ps, cam, pal, 0)
     o = oracle_render(ps, cam, pal, 0)
     _compare_frame(g, o)
-    assert g.info.status == 0 and g.info.visible == 100_000
+    # a few sub-pixel footprints reach no pixel centre and are culled (C12's box)
+    assert g.info.status == 0 and g.info.visible == o.order.size > 99_000
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16"])
@@ -197,7 +198,9 @@ def test_depth_key_rounding(case):
     x = x.astype(np.float32)
     n = x.size
     sp = [synth.Species(0, n, use_log=0, brightness=1.0, absorption=0.05)]
-    ps = _ps(x, y, np.zeros(n), np.full(n, 1e-3), rng.uniform(0.5, 1.0, n), sp)
+    # h grows with the distance so that each footprint (~1.5 px) reaches a pixel centre
+    h = (0.02 * np.abs(x.astype(np.float64)) + 1e-3).astype(np.float32)
+    ps = _ps(x, y, np.zeros(n), h, rng.uniform(0.5, 1.0, n), sp)
     for mode in (1, 0):
         g = gpu_render(ps, cam, pal, mode)
         o = oracle_render(ps, cam, pal, mode)
@@ -209,7 +212,10 @@ def test_depth_key_rounding(case):
         want = np.where(k % 2 == 0, x[:1000], np.nextafter(x[:1000], np.float32(np.inf)))
         np.testing.assert_array_equal(key, want.view(np.uint32))
     else:
-        assert (g.key[:2] == np.uint32(0x7F800000)).all()   # beyond the float range: +inf
+        # beyond the float range the depth rounds to +inf, so 1/Z = 0 and the footprint has no
+        # radius: those particles reach no pixel and are culled (the key rounding itself is
+        # tested on the host, tests/test_ieee754.py)
+        assert (g.key[:2] == np.uint32(0xFFFFFFFF)).all() and (g.key[2:4] != np.uint32(0xFFFFFFFF)).all()
 
 
 @pytest.mark.slow

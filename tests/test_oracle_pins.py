@@ -110,8 +110,9 @@ def test_basis_orthonormal_any_view(oracle_mod):
         B = np.array([c.right[:], c.upv[:], c.fwd[:]])
         np.testing.assert_allclose(B @ B.T, np.eye(3), atol=1e-14)
         assert np.linalg.det(B) == pytest.approx(1.0, abs=1e-14)  # right-handed (right, up, forward)
-        geo = O.geometry(cam, [0.5], [0.5], [0.5], [0.001])
-        assert abs(geo.sx[0] - 32) < 1e-4 and abs(geo.sy[0] - 24) < 1e-4
+        # h large enough for the footprint to reach a pixel centre (else the particle is culled)
+        geo = O.geometry(cam, [0.5], [0.5], [0.5], [0.05])
+        assert geo.visible[0] and abs(geo.sx[0] - 32) < 1e-4 and abs(geo.sy[0] - 24) < 1e-4
 
 
 def test_depth_key_axis_camera_is_z_plus_distance(oracle_mod):
@@ -520,3 +521,43 @@ def test_selected_pixels_equal_whole_image_and_brute_force(oracle_mod, tile):
         sel = O.render_frame(ps, cam, pal, mode, tile=tile, trunc_f=40.0, pixels=pix).image
         ref = _numpy_brute(fr.geo, fr.E, fr.A, fr.order, W, H, mode)
         np.testing.assert_allclose(sel, ref[pix[:, 1], pix[:, 0]], rtol=1e-12, atol=1e-14)
+
+
+def test_tight_box_holds_every_pixel_the_cut_admits(oracle_mod):
+    """The box (C12) is only a search structure: the tiled render must equal
+    the untiled brute force (every pixel against every particle with the same
+    single-precision cut) bit for bit.  Particles are put where the box's
+    edges are closest to a pixel centre: centres on and next to pixel centres
+    and edges, radii at and just around integers and half-integers, so that
+    (sx -/+ r) - 1/2 lands on, or within a few ulp of, an integer."""
+    O = oracle_mod
+    W, H = 40, 28
+    cam = _axis_cam(W, H, 45.0)
+    c = O.camera(cam)
+    s = c.scale
+    rng = np.random.default_rng(77)
+    n = 600
+    # screen positions and radii in pixels, then back to world coordinates at depth Z
+    Z = rng.uniform(1.2, 2.4, n)
+    px = rng.integers(2, W - 2, n) + rng.choice([0.0, 0.5, 1e-6, -1e-6, 0.5 + 1e-6, 0.5 - 1e-6], n)
+    py = rng.integers(2, H - 2, n) + rng.choice([0.0, 0.5, 1e-6, -1e-6], n)
+    rpx = rng.integers(0, 4, n) + rng.choice([0.5, 1.0, 0.5 + 2e-6, 1.0 - 2e-6, 0.3], n)
+    x = 0.5 + (px - W / 2) * Z / s
+    y = 0.5 - (py - H / 2) * Z / s
+    z = Z - 1.5
+    h = rpx * Z / s / 2.0                      # r = f sigma_pix with f = 2, sigma = h
+    ps = _ps(x, y, z, h, rng.lognormal(0, 1, n))
+    pal = synth.colormap()
+    for tile in (4, 8):
+        fr = O.render_frame(ps, cam, pal, 0, tile=tile)
+        brute = O.render_brute(fr.geo, fr.E, fr.A, fr.order, W, H, 0)
+        np.testing.assert_array_equal(fr.image, brute)
+    # the particles culled for an empty box (all are in front of the camera
+    # and on screen) have no pixel centre clearly inside their disc
+    geo = O.geometry(cam, ps.x, ps.y, ps.z, ps.h)
+    off = np.nonzero(~geo.visible)[0]
+    assert off.size > 0 and geo.visible.sum() > n // 2
+    jj, ii = np.meshgrid(np.arange(H) + 0.5, np.arange(W) + 0.5, indexing="ij")
+    for p in off:
+        d2 = (ii - px[p]) ** 2 + (jj - py[p]) ** 2
+        assert not (d2 < (rpx[p] * (1 - 1e-4) - 1e-4) ** 2).any(), p
