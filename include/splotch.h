@@ -324,8 +324,9 @@ typedef struct {
  * or independent snapshots) in one persistent launch: as many CTAs as fit on
  * the GPU take (frame, tile) tasks from `counter` (device, one uint32 owned
  * by the caller; zeroed by this call on `stream`), larger frames first.  Each
- * frame's image equals what splotch_render_tiles gives for it.  The frames'
- * workspaces must be distinct.  Makes no allocation and no host
+ * frame's image equals what splotch_render_tiles gives for it with
+ * register staging, no early termination and no partial image (the batch
+ * items carry no such settings).  The frames' workspaces must be distinct.  Makes no allocation and no host
  * synchronisation, so a sequence of these calls can be captured in a CUDA
  * graph.  SPLOTCH_ERR_ARG for a bad item, a tile size other than 8, 16 or
  * 32, or more than SPLOTCH_MAX_BATCH items.

@@ -65,7 +65,7 @@ __device__ __forceinline__ ushort4 unpack_tile_box(uint32_t v) {
 __global__ void __launch_bounds__(256) k_bin_reduce_pay(BinArgs a) {
     __shared__ unsigned long long ws[9];
     const uint32_t n = a.hdr->visible;
-    const uint32_t *pay = a.hdr->sorted_buf ? a.pay[1] : a.pay[0];
+    const uint32_t *pay = a.hdr->sorted_buf ? a.pk[1] : a.pk[0];
     uint64_t beg, end;
     bin_range(a.ctas, n, &beg, &end);
     unsigned long long sum = 0;
@@ -89,6 +89,9 @@ __global__ void __launch_bounds__(256) k_bin_reduce_pay(BinArgs a) {
     if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
 }
 
+// PACKED: the transform's packed tile boxes (4 B) are gathered and stored
+// packed; otherwise the 8 B pixel boxes are gathered and converted.
+template <bool PACKED>
 __global__ void __launch_bounds__(256) k_bin_reduce(BinArgs a) {
     __shared__ unsigned long long ws[9];
     const uint32_t n = a.hdr->visible;
@@ -108,19 +111,22 @@ __global__ void __launch_bounds__(256) k_bin_reduce(BinArgs a) {
             p[u] = k < end ? list[k] : 0xFFFFFFFFu;
         }
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u)
-            b[u] = p[u] != 0xFFFFFFFFu && SPL_CHECK(a.hdr, p[u] < a.hdr->layout.n) ? a.box[p[u]]
-                                                                                   : make_ushort4(1, 1, 0, 0);
+        for (int u = 0; u < kIlp; ++u) {
+            const bool ok = p[u] != 0xFFFFFFFFu && SPL_CHECK(a.hdr, p[u] < a.hdr->layout.n);
+            if (PACKED) b[u] = unpack_tile_box(ok ? a.tbox[p[u]] : 0x000000FFu);
+            else b[u] = ok ? a.box[p[u]] : make_ushort4(1, 1, 0, 0);
+        }
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             const uint64_t k = k0 + (uint64_t)u * blockDim.x + threadIdx.x;
             if (k >= end) continue;
             // the particle's box in tiles, stored in list order for the emission
-            const ushort4 t = b[u].x > b[u].z ? make_ushort4(1, 1, 0, 0)
-                                              : make_ushort4(b[u].x >> a.tshift, b[u].y >> a.tshift,
-                                                             b[u].z >> a.tshift, b[u].w >> a.tshift);
+            const ushort4 t = PACKED || b[u].x > b[u].z ? b[u]
+                                                         : make_ushort4(b[u].x >> a.tshift, b[u].y >> a.tshift,
+                                                                        b[u].z >> a.tshift, b[u].w >> a.tshift);
             if (t.x <= t.z) sum += cells_of(t, kSuperShift);
-            a.sbox[k] = t;
+            if (PACKED) a.psbox[k] = (uint32_t)t.x | ((uint32_t)t.y << 8) | ((uint32_t)t.z << 16) | ((uint32_t)t.w << 24);
+            else a.sbox[k] = t.x <= t.z ? t : make_ushort4(1, 1, 0, 0);
         }
     }
     unsigned long long tot;
@@ -169,7 +175,9 @@ __global__ void __launch_bounds__(1024) k_bin_scan(BinArgs a) {
 // thread per round.  A thread finds its cell's warp from the warp totals and
 // its particle by binary search over the segment's first cells, so the work
 // is balanced whatever the particles' sizes.
-template <bool PAY>
+// PACKED: the tile boxes in render order are packed (a.pk: the depth sort's
+// payload or the count pass's packed copy); otherwise a.sbox.
+template <bool PACKED>
 __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
     constexpr int kRounds = kBinStep / 256;
     __shared__ uint32_t s_lp[kBinStep];       // large particles, per warp segment of 256, in list order
@@ -179,7 +187,7 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
     __shared__ uint32_t s_wtot[3][8];         // per warp: cells, large particles, large cells
     const uint32_t n = a.hdr->visible;
     const uint32_t *list = a.hdr->sorted_buf ? a.list[1] : a.list[0];
-    const uint32_t *pay = a.hdr->sorted_buf ? a.pay[1] : a.pay[0];
+    const uint32_t *pk = a.hdr->sorted_buf ? a.pk[1] : a.pk[0];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t beg, end;
     bin_range(a.ctas, n, &beg, &end);
@@ -200,7 +208,7 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
             tb[q] = make_ushort4(1, 1, 0, 0);
             if (j < m) {
                 p[q] = list[step + j];
-                tb[q] = PAY ? unpack_tile_box(pay[step + j]) : a.sbox[step + j];
+                tb[q] = PACKED ? unpack_tile_box(pk[step + j]) : a.sbox[step + j];
                 if (tb[q].x <= tb[q].z) nt[q] = cells_of(tb[q], kSuperShift);
             }
             const bool big = nt[q] > a.large_tiles;
@@ -680,8 +688,15 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     a.hdr = hdr;
     a.list[0] = at<uint32_t>(ws, L.off_sv[0]);
     a.list[1] = at<uint32_t>(ws, L.off_sv[1]);
-    a.pay[0] = at<uint32_t>(ws, L.off_pay[0]);
-    a.pay[1] = at<uint32_t>(ws, L.off_pay[1]);
+    const bool pay = tile_payload(L), packed = tile_box_packs(L);
+    a.tbox = packed ? at<uint32_t>(ws, L.off_tbox) : nullptr;
+    a.psbox = at<uint32_t>(ws, L.off_sbox);
+    if (pay) {
+        a.pk[0] = at<uint32_t>(ws, L.off_pay[0]);
+        a.pk[1] = at<uint32_t>(ws, L.off_pay[1]);
+    } else {
+        a.pk[0] = a.pk[1] = a.psbox;
+    }
     a.box = at<ushort4>(ws, L.off_box);
     a.sbox = at<ushort4>(ws, L.off_sbox);
     a.tshift = tshift;
@@ -692,12 +707,14 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     a.cap = L.cap;
     a.nsx = (int)L.nsx;
     a.large_tiles = large_tiles;
-    // the depth sort carried each particle's tile box when the tile counts fit its payload
-    const bool pay = tile_payload(L);
+    // the depth sort carried each particle's tile box (large frames), or the count pass
+    // gathers the transform's packed tile boxes (the pixel boxes when the tile counts do
+    // not fit 8 bits)
     if (pay) k_bin_reduce_pay<<<a.ctas, 256, 0, st>>>(a);
-    else k_bin_reduce<<<a.ctas, 256, 0, st>>>(a);
+    else if (packed) k_bin_reduce<true><<<a.ctas, 256, 0, st>>>(a);
+    else k_bin_reduce<false><<<a.ctas, 256, 0, st>>>(a);
     k_bin_scan<<<1, 1024, 0, st>>>(a);
-    if (pay) k_bin_emit<true><<<a.ctas, 256, 0, st>>>(a);
+    if (packed) k_bin_emit<true><<<a.ctas, 256, 0, st>>>(a);
     else k_bin_emit<false><<<a.ctas, 256, 0, st>>>(a);
     count_launches(3);
     cudaError_t e = cudaGetLastError();

@@ -32,6 +32,7 @@ struct Layout {
     uint32_t pad0;
     uint64_t off_geo, off_col, off_key, off_box, off_sbox;   // geo: {sx, sy, r2, -log2(e)/sigma_pix^2}; col: {Er, Eg, Eb, A}
     uint64_t off_pay[2];     // tile-box payload of the depth sort (ping-pong), inside the sbox section
+    uint64_t off_tbox;       // packed tile box per particle (index order), written by the transform
     uint64_t off_sk[2], off_sv[2];
     uint64_t off_part;
     uint64_t off_hist, off_htot;
@@ -107,6 +108,8 @@ struct TransformArgs {
     float sigma_per_h, trunc_f;
     int slab;                  // keep only slab_lo <= key < slab_hi
     uint32_t slab_lo, slab_hi;
+    uint32_t *tbox;            // packed tile boxes (nullptr: the tile counts do not fit 8 bits)
+    int tshift;                // log2(tile side)
 };
 
 struct ColorizeArgs {
@@ -137,13 +140,10 @@ struct RadixPass {
     uint32_t hist_stride;
     uint32_t *htot;            // [256]
     Header *hdr;
-    // Optional payload carried with each item (nullptr pay_out: none).  The
-    // first pass over particles makes it from the particle's pixel box
-    // (box_in, index order): its box in tiles, 8 bits per edge.
-    const ushort4 *box_in;
+    // Optional payload carried with each item (nullptr pay_out: none); the
+    // first pass over particles reads it in index order, like the keys.
     const uint32_t *pay_in;
     uint32_t *pay_out;
-    int tshift;                // log2(tile side), for box_in
 };
 
 // Emission of (super-tile, particle) entries in render order.
@@ -159,7 +159,9 @@ struct BinArgs {
     const uint32_t *list[2];   // ordered visible list candidates (sorted_buf selects)
     const ushort4 *box;
     ushort4 *sbox;             // tile-level box per ordered position (written by the reduce, read by the emission)
-    const uint32_t *pay[2];    // or: the packed tile box carried through the depth sort (sorted_buf selects)
+    const uint32_t *tbox;      // packed tile boxes per particle (index order), or nullptr
+    uint32_t *psbox;           // packed tile box per ordered position (the sbox section), when tbox is used
+    const uint32_t *pk[2];     // packed tile boxes in render order read by the emission (sorted_buf selects)
     int tshift;                // log2(tile side)
     uint64_t *part;            // per-CTA partial sums
     uint32_t ctas;
@@ -229,12 +231,14 @@ void count_launches(uint64_t k);
 cudaError_t launch_init_header(void *ws, const Layout &L, int n_species, int mode, cudaStream_t st);
 cudaError_t launch_transform(const TransformArgs &a, void *ws, const Layout &L, cudaStream_t st);
 cudaError_t launch_colorize(const ColorizeArgs &a, void *ws, const Layout &L, cudaStream_t st);
+// Tile boxes fit 32 bits (8 bits per edge) when both tile counts are at most 256.
+inline bool tile_box_packs(const Layout &L) { return L.ntx <= 256 && L.nty <= 256; }
+
 // L2 cache size of the current device (bytes).
 uint64_t device_l2_bytes();
 
 // Whether the depth sort carries each visible particle's tile box for the
-// binning (a 32-bit payload, 8 bits per edge, so both tile counts must be at
-// most 256).  It replaces binning's one random gather (the box of each
+// binning (the packed 32-bit form).  It replaces binning's one random gather (the box of each
 // particle in render order) by sequential reads, at the price of a third
 // array in every sort pass; that pays only when the boxes (8 B per particle)
 // do not stay in L2.
@@ -243,7 +247,7 @@ uint64_t device_l2_bytes();
 // it to cover both at small sizes).
 int tile_payload_override();   // -1: automatic, 0 or 1: forced
 inline bool tile_payload(const Layout &L) {
-    if (!(L.ntx <= 256 && L.nty <= 256)) return false;
+    if (!tile_box_packs(L)) return false;
     const int o = tile_payload_override();
     return o >= 0 ? o == 1 : L.n * 8 > device_l2_bytes();
 }

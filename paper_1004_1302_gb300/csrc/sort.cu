@@ -125,13 +125,6 @@ constexpr int kDsMinBlocksPay = 2;
 constexpr int kDsWarps = kDsThreads / 32;
 constexpr int kDsItems = kSortTile / kDsThreads;
 
-// The packed tile box of a particle (8 bits per edge: x0, y0, x1, y1 in
-// tiles) from its pixel box.
-__device__ __forceinline__ uint32_t pack_tile_box(const ushort4 b, int tshift) {
-    return (uint32_t)(b.x >> tshift) | ((uint32_t)(b.y >> tshift) << 8) | ((uint32_t)(b.z >> tshift) << 16) |
-           ((uint32_t)(b.w >> tshift) << 24);
-}
-
 template <bool PAY>
 __global__ void __launch_bounds__(kDsThreads, PAY ? kDsMinBlocksPay : kDsMinBlocks) k_radix_downsweep(RadixPass P) {
     __shared__ uint32_t skey[kSortTile];
@@ -168,11 +161,7 @@ __global__ void __launch_bounds__(kDsThreads, PAY ? kDsMinBlocksPay : kDsMinBloc
             const uint64_t i = wbase + r * 32 + lane;
             key[r] = i < end ? P.key_in[i] : kInvalidKey;
             val[r] = i < end ? (P.val_in ? P.val_in[i] : (uint32_t)i) : 0u;
-            if (PAY) {
-                // the first pass makes the payload from the pixel box, only for the items it keeps
-                if (P.box_in) pay[r] = i < end && key[r] != kInvalidKey ? pack_tile_box(P.box_in[i], P.tshift) : 0u;
-                else pay[r] = i < end ? P.pay_in[i] : 0u;
-            }
+            if (PAY) pay[r] = i < end ? P.pay_in[i] : 0u;   // the first pass reads the transform's packed tile boxes
         }
 #pragma unroll
         for (int r = 0; r < kDsItems; ++r) {
@@ -291,9 +280,8 @@ cudaError_t launch_sort(void *ws, const Layout &L, int mode, cudaStream_t st) {
     // it in render order instead of gathering it by index
     const bool pay = tile_payload(L);
     if (pay) {
-        p.box_in = at<ushort4>(ws, L.off_box);
+        p.pay_in = at<uint32_t>(ws, L.off_tbox);
         p.pay_out = at<uint32_t>(ws, L.off_pay[0]);
-        p.tshift = L.tile == 8 ? 3 : (L.tile == 16 ? 4 : 5);
     }
     cudaError_t e = L.n ? launch_radix_pass(p, st) : cudaSuccess;
     if (e != cudaSuccess) return e;
@@ -310,7 +298,6 @@ cudaError_t launch_sort(void *ws, const Layout &L, int mode, cudaStream_t st) {
             q.depth_pass = pass;
             q.skip_invalid = 0;
             if (pay) {
-                q.box_in = nullptr;
                 q.pay_in = at<uint32_t>(ws, L.off_pay[(pass - 1) & 1]);
                 q.pay_out = at<uint32_t>(ws, L.off_pay[pass & 1]);
             }

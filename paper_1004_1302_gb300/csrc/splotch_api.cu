@@ -74,6 +74,7 @@ int compute_layout(uint64_t n, int width, int height, int tile, uint64_t cap, La
     L.off_col = take(n * 16);
     L.off_key = take(n * 4);
     L.off_box = take(n * 8);
+    L.off_tbox = take(n * 4);
     L.off_sbox = take(n * 8 + 256);
     L.off_pay[0] = L.off_sbox;
     L.off_pay[1] = L.off_sbox + align256(n * 4);
@@ -251,6 +252,8 @@ int splotch_transform(const splotch_particles *p, const splotch_camera *cam, con
     a.slab = params->slab != 0;
     a.slab_lo = params->slab_key_lo;
     a.slab_hi = params->slab_key_hi;
+    a.tshift = L.tile == 8 ? 3 : (L.tile == 16 ? 4 : 5);
+    a.tbox = tile_box_packs(L) ? at<uint32_t>(workspace, L.off_tbox) : nullptr;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_init_header(workspace, L, p->n_species, params->mode, st);
     if (e == cudaSuccess) e = launch_transform(a, workspace, L, st);

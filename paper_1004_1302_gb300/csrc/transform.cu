@@ -117,6 +117,13 @@ __global__ void __launch_bounds__(256) k_transform(TransformArgs a, float4 *geo,
             geo[i] = f.geo;
             key[i] = f.key;
             box[i] = f.box;
+            if (a.tbox) {
+                // the box in tiles, 8 bits per edge (what binning reads); x0 > x1 when culled
+                a.tbox[i] = f.key == kInvalidKey
+                                ? 0x000000FFu
+                                : (uint32_t)(f.box.x >> a.tshift) | ((uint32_t)(f.box.y >> a.tshift) << 8) |
+                                      ((uint32_t)(f.box.z >> a.tshift) << 16) | ((uint32_t)(f.box.w >> a.tshift) << 24);
+            }
             if (f.key != kInvalidKey) {
                 nvis += 1;
                 kmin = min(kmin, f.key);
