@@ -141,10 +141,27 @@ __global__ void __launch_bounds__(256) k_transform(TransformArgs a, float4 *geo,
     }
 }
 
-// Range pre-pass of one quantity of one species: min/max of u (log10 of the
-// value, or the value) into two of the header's order-preserving slots.
-__global__ void __launch_bounds__(256) k_range(const void *v, int dtype, uint64_t begin, uint64_t end, int use_log,
-                                               uint32_t *lo_enc, uint32_t *hi_enc) {
+// Range pre-pass: min/max of u (log10 of the value, or the value) of one
+// quantity of one species into two of the header's order-preserving slots.
+// Every quantity that needs a range is one job, all jobs in one launch
+// (blockIdx.y).
+struct RangeJob {
+    const void *v;
+    uint64_t begin, end;
+    uint32_t *lo_enc, *hi_enc;
+    int use_log;
+};
+constexpr int kMaxRangeJobs = SPLOTCH_MAX_SPECIES * 5;
+struct RangeJobs {
+    RangeJob job[kMaxRangeJobs];
+    int dtype;
+};
+
+__global__ void __launch_bounds__(256) k_range(const __grid_constant__ RangeJobs jobs) {
+    const RangeJob &J = jobs.job[blockIdx.y];
+    const void *v = J.v;
+    const int dtype = jobs.dtype, use_log = J.use_log;
+    const uint64_t begin = J.begin, end = J.end;
     float lo = INFINITY, hi = -INFINITY;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     // four independent loads in flight per thread
@@ -167,8 +184,8 @@ __global__ void __launch_bounds__(256) k_range(const void *v, int dtype, uint64_
     uint32_t elo = __reduce_min_sync(0xFFFFFFFFu, float_to_ordered(lo));
     uint32_t ehi = __reduce_max_sync(0xFFFFFFFFu, float_to_ordered(hi));
     if (lane_id() == 0) {
-        atomicMin(lo_enc, elo);
-        atomicMax(hi_enc, ehi);
+        atomicMin(J.lo_enc, elo);
+        atomicMax(J.hi_enc, ehi);
     }
 }
 
@@ -301,32 +318,32 @@ cudaError_t launch_transform(const TransformArgs &a, void *ws, const Layout &L, 
 
 cudaError_t launch_colorize(const ColorizeArgs &a, void *ws, const Layout &L, cudaStream_t st) {
     const int sms = sm_count();
-    for (int s = 0; s < a.n_species; ++s) {
-        const splotch_species &sp = a.sp[s];
-        const uint64_t b = a.begin[s], e = a.begin[s + 1];
-        if (e <= b || !(isnan(sp.lo) || isnan(sp.hi))) continue;
-        uint64_t blocks = (e - b + 255) / 256;
-        int grid = (int)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);
-        k_range<<<grid, 256, 0, st>>>(a.v, a.dtype, b, e, sp.use_log, &header(ws)->range_lo_enc[s],
-                                       &header(ws)->range_hi_enc[s]);
-        count_launches(1);
-    }
+    static thread_local RangeJobs jobs;
+    int nj = 0;
+    uint64_t longest = 0;
+    Header *h = header(ws);
+    auto add = [&](const void *v, uint64_t b, uint64_t e, int use_log, uint32_t *lo, uint32_t *hi) {
+        jobs.job[nj++] = RangeJob{v, b, e, lo, hi, use_log};
+        if (e - b > longest) longest = e - b;
+    };
     for (int s = 0; s < a.n_species; ++s) {
         const splotch_species &sp = a.sp[s];
         const uint64_t b = a.begin[s], e = a.begin[s + 1];
         if (e <= b) continue;
-        uint64_t blocks = (e - b + 255) / 256;
-        int grid = (int)(blocks < (uint64_t)sms * 4 ? blocks : (uint64_t)sms * 4);
+        if (isnan(sp.lo) || isnan(sp.hi)) add(a.v, b, e, sp.use_log, &h->range_lo_enc[s], &h->range_hi_enc[s]);
         if (sp.use_vector)
-            for (int c = 0; c < 3; ++c) {
-                k_range<<<grid, 256, 0, st>>>(a.vec[c], a.dtype, b, e, 0, &header(ws)->vlo_enc[s][c],
-                                               &header(ws)->vhi_enc[s][c]);
-                count_launches(1);
-            }
-        if (sp.modulate) {
-            k_range<<<grid, 256, 0, st>>>(a.q, a.dtype, b, e, 0, &header(ws)->qlo_enc[s], &header(ws)->qhi_enc[s]);
-            count_launches(1);
-        }
+            for (int c = 0; c < 3; ++c) add(a.vec[c], b, e, 0, &h->vlo_enc[s][c], &h->vhi_enc[s][c]);
+        if (sp.modulate) add(a.q, b, e, 0, &h->qlo_enc[s], &h->qhi_enc[s]);
+    }
+    if (nj) {
+        jobs.dtype = a.dtype;
+        // about eight CTAs per SM in all, shared by the jobs; none gets more CTAs than its
+        // values fill
+        const uint64_t want = (longest + 4 * 256 - 1) / (4 * 256);
+        const uint64_t share = (uint64_t)sms * 8 / (uint64_t)nj;
+        const unsigned gx = (unsigned)(want < share ? want : (share ? share : 1));
+        k_range<<<dim3(gx ? gx : 1, (unsigned)nj), 256, 0, st>>>(jobs);
+        count_launches(1);
     }
     k_range_finish<<<1, 32, 0, st>>>(header(ws), a);
     count_launches(1);
