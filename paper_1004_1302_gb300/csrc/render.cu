@@ -51,8 +51,6 @@ template <int B> struct TmaSmem {
     __align__(8) unsigned long long bar[kTmaStages];
 };
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
 __device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, uint32_t r0, uint32_t r1, uint32_t r2,
                                             uint32_t r3, unsigned long long *bar) {
     asm volatile(
@@ -61,21 +59,6 @@ __device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, u
         :: "r"(smem_addr(dst)), "l"(map), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_addr(bar))
         : "memory");
 }
-
-// Wait for phase `parity` of an mbarrier, at most `limit` polls; false if
-// the limit ran out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, uint32_t limit) {
-    for (uint32_t it = 0; it < limit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-            : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-constexpr uint32_t kTmaWaitPolls = 1u << 22;   // each try_wait blocks a while: far beyond any copy's time
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -412,13 +395,12 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
             if (threadIdx.x < 32) {
                 const uint32_t ng = (nb + 3) / 4;
                 if (threadIdx.x == 0) {
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                                 :: "r"(smem_addr(&ts->bar[stage])), "r"(ng * 128u) : "memory");
+                    mbar_arrive_expect_tx(&ts->bar[stage], ng * 128u);
                 }
                 __syncwarp();
                 // the stage's previous records were read by generic loads before the barrier that
                 // precedes this call: order them before the copies that overwrite them
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                fence_proxy_async_smem();
                 for (uint32_t g = threadIdx.x; g < ng; g += 32) {
                     uint32_t r[4];
 #pragma unroll
@@ -458,7 +440,7 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
     auto store = [&](int buf, uint32_t base, int stage) {
         const uint32_t nb = min((uint32_t)B, end - base);
         if constexpr (TMA) {
-            if (!mbar_wait(&ts->bar[stage], (nstored / kTmaStages) & 1u, kTmaWaitPolls) && threadIdx.x == 0)
+            if (!mbar_wait(&ts->bar[stage], (nstored / kTmaStages) & 1u, kAsyncWaitPolls) && threadIdx.x == 0)
                 atomicExch(const_cast<int *>(&a.hdr->status), (int)SPLOTCH_ERR_TIMEOUT);
             nstored += 1;
         }
@@ -489,7 +471,7 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
     if constexpr (TMA) {
         if (threadIdx.x == 0) {
             for (int k = 0; k < kTmaStages; ++k)
-                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&ts->bar[k])) : "memory");
+                mbar_init(&ts->bar[k]);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
         __syncthreads();
@@ -617,7 +599,7 @@ __device__ __forceinline__ void render_tile4(const RenderArgs &a, const int tile
                     uint32_t k = nstored;
                     int st = nstage;
                     for (uint32_t b2 = next; b2 < end && b2 < base + (uint32_t)kTmaStages * B; b2 += B, ++k) {
-                        mbar_wait(&ts->bar[st], (k / kTmaStages) & 1u, kTmaWaitPolls);
+                        mbar_wait(&ts->bar[st], (k / kTmaStages) & 1u, kAsyncWaitPolls);
                         st = st + 1 == kTmaStages ? 0 : st + 1;
                     }
                 }
