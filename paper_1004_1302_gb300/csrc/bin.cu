@@ -383,8 +383,18 @@ __global__ void __launch_bounds__(256) k_fine_count(FineArgs a) {
     const uint4 un = a.units[u];
     if (threadIdx.x < (kSuperSide + 1) * (kSuperSide + 1)) (&diff[0][0])[threadIdx.x] = 0;
     __syncthreads();
-    for (uint32_t i = un.y + threadIdx.x; i < un.z; i += 256) {
-        const FineRect f = key_rect(a.skey[i]);
+    // a unit is at most kUnit = 8 x 256 entries: every thread's loads are in flight together
+    static_assert(kUnit <= 8 * 256, "one load per thread and round");
+    uint32_t key[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const uint32_t i = un.y + threadIdx.x + 256u * r;
+        key[r] = i < un.z ? a.skey[i] : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        if (un.y + threadIdx.x + 256u * r >= un.z) continue;
+        const FineRect f = key_rect(key[r]);
         atomicAdd(&diff[f.r0][f.c0], 1);
         atomicAdd(&diff[f.r0][f.c1 + 1], -1);
         atomicAdd(&diff[f.r1 + 1][f.c0], -1);

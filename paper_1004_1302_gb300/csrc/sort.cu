@@ -62,25 +62,35 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(RadixPass P) {
     const uint32_t warp = threadIdx.x >> 5;
     uint64_t beg, end;
     cta_range(P, n, &beg, &end);
-    for (uint64_t base = beg; base < end; base += 4 * kSortThreads) {
-        const uint64_t i = base + 4 * threadIdx.x;
-        uint32_t k[4];
-        if (i + 4 <= end) {
-            uint4 v = *reinterpret_cast<const uint4 *>(P.key_in + i);
-            k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
-        } else {
+    // a tile of kSortTile keys per step: every thread's four 16-byte loads are
+    // in flight together (one load per step left the pass waiting on latency)
+    constexpr int kLoads = kSortTile / (4 * kSortThreads);
+    for (uint64_t base = beg; base < end; base += kSortTile) {
+        uint32_t k[kLoads][4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) k[q] = i + q < end ? P.key_in[i + q] : kInvalidKey;
+        for (int l = 0; l < kLoads; ++l) {
+            const uint64_t i = base + 4 * ((uint64_t)l * kSortThreads + threadIdx.x);
+            if (i + 4 <= end) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(P.key_in + i);
+                k[l][0] = v.x; k[l][1] = v.y; k[l][2] = v.z; k[l][3] = v.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) k[l][q] = i + q < end ? P.key_in[i + q] : kInvalidKey;
+            }
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint32_t d = kRadix;
-            if (i + q < end && !(P.skip_invalid && k[q] == kInvalidKey)) d = ((k[q] - kmin) >> P.shift) & P.mask;
-            const uint32_t d0 = __shfl_sync(0xFFFFFFFFu, d, 0);
-            if (__all_sync(0xFFFFFFFFu, d == d0)) {
-                if (lane_id() == 0 && d0 < (uint32_t)kRadix) cnt[warp][d0] += 32;
-            } else if (d < (uint32_t)kRadix) {
-                atomicAdd(&cnt[warp][d], 1u);
+        for (int l = 0; l < kLoads; ++l) {
+            const uint64_t i = base + 4 * ((uint64_t)l * kSortThreads + threadIdx.x);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t d = kRadix;
+                if (i + q < end && !(P.skip_invalid && k[l][q] == kInvalidKey)) d = ((k[l][q] - kmin) >> P.shift) & P.mask;
+                const uint32_t d0 = __shfl_sync(0xFFFFFFFFu, d, 0);
+                if (__all_sync(0xFFFFFFFFu, d == d0)) {
+                    if (lane_id() == 0 && d0 < (uint32_t)kRadix) cnt[warp][d0] += 32;
+                } else if (d < (uint32_t)kRadix) {
+                    atomicAdd(&cnt[warp][d], 1u);
+                }
             }
         }
     }

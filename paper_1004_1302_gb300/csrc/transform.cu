@@ -176,7 +176,9 @@ __global__ void __launch_bounds__(256) k_range(const __grid_constant__ RangeJobs
         for (int k = 0; k < 4; ++k) {
             if (i0 + k * stride >= end) continue;
             float w = u[k];
-            if (use_log) w = log10f(fmaxf(w, 1e-37f));
+            // log10 is monotonic: the range of log10(max(v, 1e-37)) is taken from the
+            // extremes of max(v, 1e-37), and the logarithm applied to those two only
+            if (use_log) w = fmaxf(w, 1e-37f);
             lo = fminf(lo, w);
             hi = fmaxf(hi, w);
         }
@@ -222,8 +224,9 @@ __global__ void k_range_finish(Header *hdr, ColorizeArgs a) {
     }
     if (!have) return;
     float lo = a.sp[s].lo, hi = a.sp[s].hi;
-    if (isnan(lo)) lo = empty ? 0.0f : ordered_to_float(hdr->range_lo_enc[s]);
-    if (isnan(hi)) hi = empty ? 0.0f : ordered_to_float(hdr->range_hi_enc[s]);
+    const bool lg = a.sp[s].use_log;
+    if (isnan(lo)) lo = empty ? 0.0f : (lg ? log10f(ordered_to_float(hdr->range_lo_enc[s])) : ordered_to_float(hdr->range_lo_enc[s]));
+    if (isnan(hi)) hi = empty ? 0.0f : (lg ? log10f(ordered_to_float(hdr->range_hi_enc[s])) : ordered_to_float(hdr->range_hi_enc[s]));
     hdr->lo[s] = lo;
     hdr->hi[s] = hi;
     if (a.sp[s].use_vector && !empty)
@@ -234,52 +237,72 @@ __global__ void k_range_finish(Header *hdr, ColorizeArgs a) {
     if (a.sp[s].modulate && !empty) hdr->qmax[s] = ordered_to_float(hdr->qhi_enc[s]);
 }
 
+// E and A of particle i of species s; u: its intensity (unused by a vector species).
+__device__ __forceinline__ float4 colorize_one(const ColorizeArgs &a, const Header *hdr, const float *pal, float kmax,
+                                               int s, uint64_t i, float u) {
+    const splotch_species &sp = a.sp[s];
+    float r, g, b;
+    if (sp.use_vector) {
+        // each component normalised linearly over the species
+        float t[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float uc = load_value(a.vec[c], a.dtype, i);
+            const float lo = hdr->vlo[s][c], hi = hdr->vhi[s][c];
+            const float tc = hi > lo ? __fdiv_rn(uc - lo, hi - lo) : 0.0f;
+            t[c] = fminf(fmaxf(tc, 0.0f), 1.0f);
+        }
+        r = t[0]; g = t[1]; b = t[2];
+    } else if (sp.use_colormap) {
+        if (sp.use_log) u = log10f(fmaxf(u, 1e-37f));
+        const float lo = hdr->lo[s], hi = hdr->hi[s];
+        float t = hi > lo ? __fdiv_rn(u - lo, hi - lo) : 0.0f;
+        t = fminf(fmaxf(t, 0.0f), 1.0f);
+        float w = t * kmax;
+        int k = min((int)floorf(w), a.n_entries - 2);
+        float fr = w - (float)k;
+        r = (1.0f - fr) * pal[3 * k + 0] + fr * pal[3 * k + 3];
+        g = (1.0f - fr) * pal[3 * k + 1] + fr * pal[3 * k + 4];
+        b = (1.0f - fr) * pal[3 * k + 2] + fr * pal[3 * k + 5];
+    } else {
+        r = sp.fixed_rgb[0]; g = sp.fixed_rgb[1]; b = sp.fixed_rgb[2];
+    }
+    float m = 1.0f;
+    if (sp.modulate) {
+        // column density scaled by q / q_max of the species: E and A alike
+        const float qm = hdr->qmax[s];
+        m = qm > 0.0f ? __fdiv_rn(load_value(a.q, a.dtype, i), qm) : 0.0f;
+        m = fminf(fmaxf(m, 0.0f), 1.0f);
+    }
+    return make_float4(m * (sp.brightness * r), m * (sp.brightness * g), m * (sp.brightness * b), m * sp.absorption);
+}
+
+// A block takes kIlp x blockDim consecutive particles per step, thread t the
+// particles t, t + blockDim, ...: the kIlp intensity loads are in flight
+// together and every store of a warp covers consecutive particles.
+template <int kIlp>
 __global__ void __launch_bounds__(256) k_colorize(ColorizeArgs a, const Header *hdr, float4 *col) {
     __shared__ float pal[SPLOTCH_MAX_PALETTE * 3];
     for (int k = threadIdx.x; k < a.n_entries * 3; k += blockDim.x) pal[k] = a.palette[k];
     __syncthreads();
     const float kmax = (float)(a.n_entries - 1);
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += (uint64_t)gridDim.x * blockDim.x) {
-        int s = 0;
-#pragma unroll 1
-        while (s + 1 < a.n_species && i >= a.begin[s + 1]) ++s;
-        const splotch_species &sp = a.sp[s];
-        float r, g, b;
-        if (sp.use_vector) {
-            // each component normalised linearly over the species
-            float t[3];
+    const uint64_t chunk = (uint64_t)kIlp * blockDim.x;
+    for (uint64_t b0 = blockIdx.x * chunk; b0 < a.n; b0 += (uint64_t)gridDim.x * chunk) {
+        float u[kIlp];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float u = load_value(a.vec[c], a.dtype, i);
-                const float lo = hdr->vlo[s][c], hi = hdr->vhi[s][c];
-                const float tc = hi > lo ? __fdiv_rn(u - lo, hi - lo) : 0.0f;
-                t[c] = fminf(fmaxf(tc, 0.0f), 1.0f);
-            }
-            r = t[0]; g = t[1]; b = t[2];
-        } else if (sp.use_colormap) {
-            float u = load_value(a.v, a.dtype, i);
-            if (sp.use_log) u = log10f(fmaxf(u, 1e-37f));
-            const float lo = hdr->lo[s], hi = hdr->hi[s];
-            float t = hi > lo ? __fdiv_rn(u - lo, hi - lo) : 0.0f;
-            t = fminf(fmaxf(t, 0.0f), 1.0f);
-            float w = t * kmax;
-            int k = min((int)floorf(w), a.n_entries - 2);
-            float fr = w - (float)k;
-            r = (1.0f - fr) * pal[3 * k + 0] + fr * pal[3 * k + 3];
-            g = (1.0f - fr) * pal[3 * k + 1] + fr * pal[3 * k + 4];
-            b = (1.0f - fr) * pal[3 * k + 2] + fr * pal[3 * k + 5];
-        } else {
-            r = sp.fixed_rgb[0]; g = sp.fixed_rgb[1]; b = sp.fixed_rgb[2];
+        for (int k = 0; k < kIlp; ++k) {
+            const uint64_t i = b0 + threadIdx.x + (uint64_t)k * blockDim.x;
+            u[k] = i < a.n && a.v ? load_value(a.v, a.dtype, i) : 0.0f;
         }
-        float m = 1.0f;
-        if (sp.modulate) {
-            // column density scaled by q / q_max of the species: E and A alike
-            const float qm = hdr->qmax[s];
-            m = qm > 0.0f ? __fdiv_rn(load_value(a.q, a.dtype, i), qm) : 0.0f;
-            m = fminf(fmaxf(m, 0.0f), 1.0f);
+        int s = 0;
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) {
+            const uint64_t i = b0 + threadIdx.x + (uint64_t)k * blockDim.x;
+            if (i >= a.n) break;
+#pragma unroll 1
+            while (s + 1 < a.n_species && i >= a.begin[s + 1]) ++s;
+            col[i] = colorize_one(a, hdr, pal, kmax, s, i, u[k]);
         }
-        col[i] = make_float4(m * (sp.brightness * r), m * (sp.brightness * g), m * (sp.brightness * b),
-                             m * sp.absorption);
     }
 }
 
@@ -348,9 +371,9 @@ cudaError_t launch_colorize(const ColorizeArgs &a, void *ws, const Layout &L, cu
     k_range_finish<<<1, 32, 0, st>>>(header(ws), a);
     count_launches(1);
     if (a.n) {
-        uint64_t blocks = (a.n + 255) / 256;
+        uint64_t blocks = (a.n + 4 * 256 - 1) / (4 * 256);
         int grid = (int)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);
-        k_colorize<<<grid, 256, 0, st>>>(a, header(ws), at<float4>(ws, L.off_col));
+        k_colorize<4><<<grid, 256, 0, st>>>(a, header(ws), at<float4>(ws, L.off_col));
         count_launches(1);
     }
     return cudaGetLastError();
