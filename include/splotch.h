@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define SPLOTCH_ABI_VERSION 3
+#define SPLOTCH_ABI_VERSION 4
 #define SPLOTCH_MAX_SPECIES 8
 #define SPLOTCH_MAX_PALETTE 256
 
@@ -142,6 +142,12 @@ typedef struct {
                                      for tiles of 16 and 32 px in the plain render (8-px tiles, partial
                                      images and early termination load through registers).  The image is
                                      the same bit for bit either way */
+    int32_t keep_pixel_boxes;     /* 1: the transform also stores every particle's pixel box (8 B each)
+                                     for splotch_get_keys.  0 (default): it stores them only when binning
+                                     reads them (more than 256 tiles in a row or column); otherwise
+                                     binning reads the packed tile boxes, the pass writes 8 B less per
+                                     particle, and a box request to splotch_get_keys is refused with
+                                     SPLOTCH_ERR_STATE.  Nothing else depends on it */
 } splotch_render_params;
 
 /* Result summary read back by splotch_frame_info (synchronises the stream). */
@@ -286,6 +292,8 @@ int splotch_frame_info(const void *workspace, size_t workspace_bytes, splotch_fr
  * recorded by splotch_transform, then enqueues device-to-device copies.
  * splotch_get_keys: key (n x uint32, 0xFFFFFFFF when culled) and box
  *   (n x 4 int32: x0, y0, x1, y1; 0, 0, -1, -1 when culled); either may be NULL.
+ *   A box request after a transform that did not store the pixel boxes
+ *   (splotch_render_params.keep_pixel_boxes) returns SPLOTCH_ERR_STATE.
  * splotch_get_geometry: sx, sy, r2 (n floats each; 0 when culled); any may be NULL.
  * splotch_get_order: the V visible particle indices in render order.
  * splotch_get_tile_lists: offsets (ntiles + 1 uint32) and list (capacity

@@ -60,6 +60,7 @@ struct Header {
     uint32_t n_species;
     uint32_t mode;
     uint32_t series_only;      // every species with particles has A <= kSeriesMaxA
+    uint32_t boxes_kept;       // the transform stored every particle's pixel box
     uint32_t check_line;       // checked builds: source line of the first failed index check (0: none)
     uint32_t range_lo_enc[SPLOTCH_MAX_SPECIES];   // order-preserving encodings for atomic min/max
     uint32_t range_hi_enc[SPLOTCH_MAX_SPECIES];
@@ -228,8 +229,8 @@ template <class T> inline T *at(void *ws, uint64_t off) {
 void count_launches(uint64_t k);
 
 // Launchers (each returns cudaGetLastError()).
-cudaError_t launch_init_header(void *ws, const Layout &L, int n_species, int mode, cudaStream_t st);
-cudaError_t launch_transform(const TransformArgs &a, void *ws, const Layout &L, cudaStream_t st);
+cudaError_t launch_init_header(void *ws, const Layout &L, int n_species, int mode, bool boxes_kept, cudaStream_t st);
+cudaError_t launch_transform(const TransformArgs &a, void *ws, const Layout &L, bool keep_boxes, cudaStream_t st);
 cudaError_t launch_colorize(const ColorizeArgs &a, void *ws, const Layout &L, cudaStream_t st);
 // Tile boxes fit 32 bits (8 bits per edge) when both tile counts are at most 256.
 inline bool tile_box_packs(const Layout &L) { return L.ntx <= 256 && L.nty <= 256; }

@@ -895,16 +895,32 @@ cudaError_t launch_compose(const float *cf, const float *tf, const float *cb, co
 
 // Number of (pixel, particle) pairs that pass the membership test, summed
 // over the visible particles (a measurement helper, not part of a frame).
-__global__ void __launch_bounds__(256) k_count_fragments(const float4 *geo, const ushort4 *box, const uint32_t *key,
-                                                         uint64_t n, unsigned long long *out) {
+// With the pixel boxes stored, the pixels tested are the box's; without
+// them, those whose centres lie within a slightly widened radius of the
+// centre, clipped to the image: a superset of the box, which holds every
+// pixel that passes, so the count is the same either way.
+__global__ void __launch_bounds__(256) k_count_fragments(const Header *hdr, const float4 *geo, const ushort4 *box,
+                                                         const uint32_t *key, uint64_t n, int width, int height,
+                                                         unsigned long long *out) {
+    const bool boxes = hdr->boxes_kept != 0;
     unsigned long long cnt = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         if (key[i] == kInvalidKey) continue;
         const float4 g = geo[i];
-        const ushort4 b = box[i];
-        for (int j = b.y; j <= b.w; ++j) {
+        int x0, x1, y0, y1;
+        if (boxes) {
+            const ushort4 b = box[i];
+            x0 = b.x; y0 = b.y; x1 = b.z; y1 = b.w;
+        } else {
+            const float rr = sqrtf(g.z) * 1.001f + 0.01f;
+            x0 = max(0, (int)ceilf(g.x - rr - 0.5f));
+            x1 = min(width - 1, (int)floorf(g.x + rr - 0.5f));
+            y0 = max(0, (int)ceilf(g.y - rr - 0.5f));
+            y1 = min(height - 1, (int)floorf(g.y + rr - 0.5f));
+        }
+        for (int j = y0; j <= y1; ++j) {
             const float dy = __fsub_rn((float)j + 0.5f, g.y);
-            for (int x = b.x; x <= b.z; ++x) {
+            for (int x = x0; x <= x1; ++x) {
                 const float dx = __fsub_rn((float)x + 0.5f, g.x);
                 cnt += __fmaf_rn(dy, dy, __fmul_rn(dx, dx)) < g.z;
             }
@@ -918,8 +934,8 @@ __global__ void __launch_bounds__(256) k_count_fragments(const float4 *geo, cons
 cudaError_t launch_count_fragments(void *ws, const Layout &L, uint64_t *out, cudaStream_t st) {
     cudaMemsetAsync(out, 0, sizeof(uint64_t), st);
     if (L.n) {
-        k_count_fragments<<<1024, 256, 0, st>>>(at<float4>(ws, L.off_geo), at<ushort4>(ws, L.off_box),
-                                                at<uint32_t>(ws, L.off_key), L.n,
+        k_count_fragments<<<1024, 256, 0, st>>>(header(ws), at<float4>(ws, L.off_geo), at<ushort4>(ws, L.off_box),
+                                                at<uint32_t>(ws, L.off_key), L.n, L.width, L.height,
                                                 reinterpret_cast<unsigned long long *>(out));
         count_launches(1);
     }

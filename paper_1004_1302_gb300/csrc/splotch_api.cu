@@ -122,6 +122,7 @@ static int check_params(const splotch_render_params *pr) {
     if (pr->slab != 0 && pr->slab != 1) return SPLOTCH_ERR_ARG;
     if (!(pr->t_min_cutoff >= 0.0f) || !(pr->t_min_cutoff < 1.0f)) return SPLOTCH_ERR_ARG;
     if (pr->staging != 0 && pr->staging != 1) return SPLOTCH_ERR_ARG;
+    if (pr->keep_pixel_boxes != 0 && pr->keep_pixel_boxes != 1) return SPLOTCH_ERR_ARG;
     return SPLOTCH_OK;
 }
 
@@ -255,8 +256,9 @@ int splotch_transform(const splotch_particles *p, const splotch_camera *cam, con
     a.tshift = L.tile == 8 ? 3 : (L.tile == 16 ? 4 : 5);
     a.tbox = tile_box_packs(L) ? at<uint32_t>(workspace, L.off_tbox) : nullptr;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_init_header(workspace, L, p->n_species, params->mode, st);
-    if (e == cudaSuccess) e = launch_transform(a, workspace, L, st);
+    const bool keep_boxes = params->keep_pixel_boxes != 0 || !a.tbox;
+    cudaError_t e = launch_init_header(workspace, L, p->n_species, params->mode, keep_boxes, st);
+    if (e == cudaSuccess) e = launch_transform(a, workspace, L, keep_boxes, st);
     return cuda_status(e);
 }
 
@@ -451,6 +453,7 @@ int splotch_get_keys(const void *workspace, size_t workspace_bytes, uint32_t *ke
     if (key && L.n && cudaMemcpyAsync(key, at<uint32_t>(ws, L.off_key), L.n * 4, cudaMemcpyDeviceToDevice, st))
         return SPLOTCH_ERR_CUDA;
     if (box && L.n) {
+        if (!h.boxes_kept) return SPLOTCH_ERR_STATE;   // the transform did not store the pixel boxes
         k_box_to_int<<<256, 256, 0, st>>>(at<ushort4>(ws, L.off_box), at<uint32_t>(ws, L.off_key),
                                           reinterpret_cast<int4 *>(box), L.n);
         count_launches(1);

@@ -7,9 +7,10 @@
 
 namespace spl {
 
-__global__ void k_init_header(Header *hdr, Layout L, int n_species, int mode) {
+__global__ void k_init_header(Header *hdr, Layout L, int n_species, int mode, uint32_t boxes_kept) {
     if (threadIdx.x != 0) return;
     hdr->magic = kMagic;
+    hdr->boxes_kept = boxes_kept;
     hdr->status = SPLOTCH_OK;
     hdr->visible = 0;
     hdr->n_large = 0;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256) k_transform(TransformArgs a, float4 *geo,
             Footprint f = footprint(a, xs[k], ys[k], zs[k], hs[k]);
             geo[i] = f.geo;
             key[i] = f.key;
-            box[i] = f.box;
+            if (box) box[i] = f.box;
             if (a.tbox) {
                 // the box in tiles, 8 bits per edge (what binning reads); x0 > x1 when culled
                 a.tbox[i] = f.key == kInvalidKey
@@ -319,18 +320,19 @@ static int sm_count() {
     return cached[dev];
 }
 
-cudaError_t launch_init_header(void *ws, const Layout &L, int n_species, int mode, cudaStream_t st) {
-    k_init_header<<<1, 32, 0, st>>>(header(ws), L, n_species, mode);
+cudaError_t launch_init_header(void *ws, const Layout &L, int n_species, int mode, bool boxes_kept, cudaStream_t st) {
+    k_init_header<<<1, 32, 0, st>>>(header(ws), L, n_species, mode, boxes_kept ? 1u : 0u);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_transform(const TransformArgs &a, void *ws, const Layout &L, cudaStream_t st) {
+cudaError_t launch_transform(const TransformArgs &a, void *ws, const Layout &L, bool keep_boxes, cudaStream_t st) {
     if (a.n == 0) return cudaGetLastError();
     const int sms = sm_count();
     float4 *geo = at<float4>(ws, L.off_geo);
     uint32_t *key = at<uint32_t>(ws, L.off_key);
-    ushort4 *box = at<ushort4>(ws, L.off_box);
+    // the pixel boxes are stored when binning reads them (no packed tile boxes) or when asked for
+    ushort4 *box = keep_boxes || !a.tbox ? at<ushort4>(ws, L.off_box) : nullptr;
     constexpr int kIlp = 4;
     const uint64_t blocks = (a.n + kIlp * 256 - 1) / (kIlp * 256);
     const int grid = (int)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);

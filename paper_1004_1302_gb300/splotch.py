@@ -105,7 +105,8 @@ class RenderParams(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tile", ctypes.c_int32), ("sigma_per_h", ctypes.c_float),
                 ("trunc_f", ctypes.c_float), ("batch", ctypes.c_int32), ("large_threshold_px", ctypes.c_int32),
                 ("max_tile_entries", ctypes.c_uint64), ("slab", ctypes.c_int32), ("slab_key_lo", ctypes.c_uint32),
-                ("slab_key_hi", ctypes.c_uint32), ("t_min_cutoff", ctypes.c_float), ("staging", ctypes.c_int32)]
+                ("slab_key_hi", ctypes.c_uint32), ("t_min_cutoff", ctypes.c_float), ("staging", ctypes.c_int32),
+                ("keep_pixel_boxes", ctypes.c_int32)]
 
 
 class BatchItem(ctypes.Structure):
@@ -421,9 +422,10 @@ def make_species(sp) -> SpeciesParams:
 
 def make_params(mode: int, tile: int = 16, batch: int = 64, sigma_per_h: float = 1.0, trunc_f: float = 2.0,
                 large_threshold_px: int = 0, max_tile_entries: int = 0, slab=None,
-                t_min_cutoff: float = 0.0, staging: int = 0) -> RenderParams:
+                t_min_cutoff: float = 0.0, staging: int = 0, keep_pixel_boxes: int = 0) -> RenderParams:
     """slab: None, or (key_lo, key_hi) to keep only depth keys in [key_lo, key_hi).
-    staging: 0 register loads, 1 TMA gather4 copies (see include/splotch.h)."""
+    staging: 0 register loads, 1 TMA gather4 copies (see include/splotch.h).
+    keep_pixel_boxes: 1 to store every particle's pixel box for splotch_get_keys."""
     p = RenderParams()
     p.mode, p.tile, p.batch = int(mode), int(tile), int(batch)
     p.sigma_per_h, p.trunc_f = float(sigma_per_h), float(trunc_f)
@@ -433,6 +435,7 @@ def make_params(mode: int, tile: int = 16, batch: int = 64, sigma_per_h: float =
         p.slab, p.slab_key_lo, p.slab_key_hi = 1, int(slab[0]), int(slab[1])
     p.t_min_cutoff = float(t_min_cutoff)
     p.staging = int(staging)
+    p.keep_pixel_boxes = int(keep_pixel_boxes)
     return p
 
 
@@ -517,7 +520,7 @@ class Frame:
     def __init__(self, dp: DeviceParticles, cam_spec, palette, mode: int, tile: int = 16, batch: int = 64,
                  sigma_per_h: float = 1.0, trunc_f: float = 2.0, large_threshold_px: int = 0,
                  max_tile_entries: int | None = None, device="cuda", slab=None, t_min_cutoff: float = 0.0,
-                 staging: int = 0):
+                 staging: int = 0, keep_pixel_boxes: bool = False):
         import torch
         self.torch = torch
         self.dp = dp
@@ -531,7 +534,7 @@ class Frame:
             ntiles = math.ceil(self.W / tile) * math.ceil(self.H / tile)
             max_tile_entries = max(4 * dp.n, 1024) + ntiles
         self.params = make_params(mode, tile, batch, sigma_per_h, trunc_f, large_threshold_px, max_tile_entries,
-                                  slab, t_min_cutoff, staging)
+                                  slab, t_min_cutoff, staging, int(bool(keep_pixel_boxes)))
         self.pstruct = dp.struct()
         self.trans = None
         self.species = [make_species(s) for s in dp.species]
@@ -614,12 +617,16 @@ class Frame:
         raise SplotchError(ERR_WORKSPACE, "frame")
 
     # test access
-    def keys(self):
+    def keys(self, boxes: bool | None = None):
+        """Depth keys, and the pixel boxes when the frame keeps them (else None);
+        boxes=True asks for them regardless (refused by the library if the
+        transform did not store them)."""
         t = self.torch
+        want = bool(self.params.keep_pixel_boxes) if boxes is None else boxes
         key = t.empty(self.dp.n, dtype=t.int32, device=self.device)
-        box = t.empty((self.dp.n, 4), dtype=t.int32, device=self.device)
+        box = t.empty((self.dp.n, 4), dtype=t.int32, device=self.device) if want else None
         splotch_get_keys(self.ws.data_ptr(), self.ws_bytes, key.data_ptr() if self.dp.n else None,
-                         box.data_ptr() if self.dp.n else None, self.stream_ptr())
+                         box.data_ptr() if (self.dp.n and want) else None, self.stream_ptr())
         return key, box
 
     def geometry(self):

@@ -41,7 +41,7 @@ def gpu_render(ps, cam, palette, mode, dtype="f32", tile=16, batch=128, large_th
     from paper_1004_1302_gb300 import splotch as S
     dp = S.upload(ps, "cuda", dtype)
     fr = S.Frame(dp, cam, palette, mode, tile=tile, batch=batch, large_threshold_px=large_threshold_px,
-                 trunc_f=trunc_f, max_tile_entries=max_tile_entries)
+                 trunc_f=trunc_f, max_tile_entries=max_tile_entries, keep_pixel_boxes=True)
     img = fr.render().cpu().numpy()
     info = fr.info()
     key, box = fr.keys()

@@ -30,7 +30,7 @@ def test_exports_every_declared_function(S):
     for name in declared:
         assert hasattr(lib, name), name
     assert set(declared) == set(S.EXPORTS)
-    assert lib.splotch_abi_version() == 3
+    assert lib.splotch_abi_version() == 4
 
 
 def test_status_strings(S):
@@ -85,6 +85,11 @@ def test_workspace_size_and_arguments(S):
         q = S.make_params(S.ABSORPTIVE, max_tile_entries=1024, **bad)
         assert lib.splotch_workspace_size(1000, ctypes.byref(cam), ctypes.byref(q), ctypes.byref(out)) == S.ERR_ARG
     q = S.make_params(S.ABSORPTIVE, max_tile_entries=1024, staging=2)
+    assert lib.splotch_workspace_size(1000, ctypes.byref(cam), ctypes.byref(q), ctypes.byref(out)) == S.ERR_ARG
+    # keeping the pixel boxes is a flag: 0 or 1
+    q = S.make_params(S.ABSORPTIVE, max_tile_entries=1024, keep_pixel_boxes=1)
+    assert lib.splotch_workspace_size(1000, ctypes.byref(cam), ctypes.byref(q), ctypes.byref(out)) == S.OK
+    q.keep_pixel_boxes = 2
     assert lib.splotch_workspace_size(1000, ctypes.byref(cam), ctypes.byref(q), ctypes.byref(out)) == S.ERR_ARG
     q = S.make_params(S.ABSORPTIVE, max_tile_entries=1024, slab=(0, 10))
     assert lib.splotch_workspace_size(1000, ctypes.byref(cam), ctypes.byref(q), ctypes.byref(out)) == S.OK
