@@ -401,11 +401,23 @@ __global__ void __launch_bounds__(256) k_fine_count(FineArgs a) {
         atomicAdd(&diff[f.r1 + 1][f.c1 + 1], 1);
     }
     __syncthreads();
+    // the 2-D prefix sum of the difference array: along each row (shuffles in
+    // groups of eight lanes), then down each column
+    __shared__ int rowp[kSuperSide][kSuperSide];
+    const int r = threadIdx.x / kSuperSide, c = threadIdx.x % kSuperSide;
     if (threadIdx.x < 64) {
-        const int r = threadIdx.x / kSuperSide, c = threadIdx.x % kSuperSide;
+        int v = diff[r][c];
+#pragma unroll
+        for (int d = 1; d < kSuperSide; d <<= 1) {
+            const int o = __shfl_up_sync(0xFFFFFFFFu, v, d, kSuperSide);
+            if (c >= d) v += o;
+        }
+        rowp[r][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) {
         int v = 0;
-        for (int rr = 0; rr <= r; ++rr)
-            for (int cc = 0; cc <= c; ++cc) v += diff[rr][cc];
+        for (int rr = 0; rr <= r; ++rr) v += rowp[rr][c];
         a.ucnt[(size_t)u * 64 + threadIdx.x] = (uint32_t)v;
     }
 }
@@ -421,8 +433,18 @@ __global__ void __launch_bounds__(1024) k_fine_unit_scan(FineArgs a) {
     const uint32_t u0 = a.ufirst[s], u1 = min(a.ufirst[s + 1], a.max_units);
     const uint32_t nu = u1 > u0 ? u1 - u0 : 0u, per = (nu + kChunks - 1) / kChunks;
     const uint32_t b = u0 + g * per, e = min(b + per, u1);
+    // eight units' counts in flight at a time (a thread walks up to thousands of units)
+    constexpr uint32_t kBatch = 8;
     uint32_t sum = 0;
-    for (uint32_t u = b; u < e; ++u) sum += a.ucnt[(size_t)u * 64 + t];
+    uint32_t u = b;
+    for (; u + kBatch <= e; u += kBatch) {
+        uint32_t v[kBatch];
+#pragma unroll
+        for (uint32_t k = 0; k < kBatch; ++k) v[k] = a.ucnt[(size_t)(u + k) * 64 + t];
+#pragma unroll
+        for (uint32_t k = 0; k < kBatch; ++k) sum += v[k];
+    }
+    for (; u < e; ++u) sum += a.ucnt[(size_t)u * 64 + t];
     part[g][t] = sum;
     __syncthreads();
     if (g == 0) {
@@ -438,7 +460,18 @@ __global__ void __launch_bounds__(1024) k_fine_unit_scan(FineArgs a) {
     }
     __syncthreads();
     uint32_t run = part[g][t];
-    for (uint32_t u = b; u < e; ++u) {
+    u = b;
+    for (; u + kBatch <= e; u += kBatch) {
+        uint32_t v[kBatch];
+#pragma unroll
+        for (uint32_t k = 0; k < kBatch; ++k) v[k] = a.ucnt[(size_t)(u + k) * 64 + t];
+#pragma unroll
+        for (uint32_t k = 0; k < kBatch; ++k) {
+            a.ucnt[(size_t)(u + k) * 64 + t] = run;
+            run += v[k];
+        }
+    }
+    for (; u < e; ++u) {
         const size_t q = (size_t)u * 64 + t;
         const uint32_t c = a.ucnt[q];
         a.ucnt[q] = run;
@@ -528,7 +561,10 @@ __global__ void __launch_bounds__(1024) k_fine_offsets(FineArgs a) {
 
 // Fine entries of one unit staged in shared memory (tile by tile) before they
 // are written out; units with more go straight to global memory.
-constexpr int kFineBuf = 8192;
+// 6144 entries (24 KB): room for seven CTAs per SM (10M binning 0.584 ->
+// 0.570 ms against 8192 entries at five CTAs; a unit holds ~3K fine entries
+// at 1.07e9 particles, ~7K at 10M; larger units write to global memory)
+constexpr int kFineBuf = 6144;
 
 // Per unit, 256 entries at a time, one entry per thread.  A warp's 32
 // entries (list order = lane order) are described by 16 ballots: for each
@@ -542,7 +578,10 @@ constexpr int kFineBuf = 8192;
 // every tile.  The unit's
 // entries of a tile form one run of the tile's list; the runs are gathered in
 // shared memory and copied out whole, so the global writes are coalesced.
-__global__ void __launch_bounds__(256) k_fine_emit(FineArgs a) {
+// Seven CTAs per SM (32 registers, no spills; 30 KB of shared memory each):
+// the expansion waits on latency more than on issue (binning 0.573 -> 0.565
+// ms at 10M, 33.0 -> 32.6 ms at 1.07e9 against 46 registers and 5 CTAs)
+__global__ void __launch_bounds__(256, 7) k_fine_emit(FineArgs a) {
     __shared__ uint32_t s_buf[kFineBuf];
     __shared__ __align__(16) uint32_t s_b[8][16];   // per warp: row ballots 0..7, column ballots 8..15
     __shared__ uint32_t s_wcnt[8][64];              // per warp: its entries meeting each fine tile
@@ -585,13 +624,24 @@ __global__ void __launch_bounds__(256) k_fine_emit(FineArgs a) {
     }
     __syncthreads();
     const bool staged = s_lb[64] <= (uint32_t)kFineBuf;
+    // each chunk's entry is loaded one chunk ahead (its key and particle), so
+    // a chunk's loads are in flight while the previous chunk is placed
+    uint32_t np = 0, nk = 0xFFFFFFFFu;
+    if (un.y + threadIdx.x < un.z) {
+        np = a.sval[un.y + threadIdx.x];
+        nk = a.skey[un.y + threadIdx.x];
+    }
     for (uint32_t i0 = un.y; i0 < un.z; i0 += 256) {
         const uint32_t i = i0 + threadIdx.x;
         uint32_t p = 0;
         FineRect f{1, 0, 1, 0};                      // empty
         if (i < un.z) {
-            p = a.sval[i];
-            f = key_rect(a.skey[i]);
+            p = np;
+            f = key_rect(nk);
+        }
+        if (i + 256 < un.z) {
+            np = a.sval[i + 256];
+            nk = a.skey[i + 256];
         }
         const uint32_t rows = f.r0 <= f.r1 ? (0xFFu >> (kSuperSide - 1 - f.r1)) & (0xFFu << f.r0) : 0u;
         const uint32_t cols = f.c0 <= f.c1 ? (0xFFu >> (kSuperSide - 1 - f.c1)) & (0xFFu << f.c0) : 0u;
