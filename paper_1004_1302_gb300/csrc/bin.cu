@@ -63,6 +63,7 @@ __device__ __forceinline__ ushort4 unpack_tile_box(uint32_t v) {
 // Count pass when the tile boxes came through the depth sort in render
 // order: a sequential read, four boxes per thread at a time.
 __global__ void __launch_bounds__(256) k_bin_reduce_pay(BinArgs a) {
+    pdl_enter();
     __shared__ unsigned long long ws[9];
     const uint32_t n = a.hdr->visible;
     const uint32_t *pay = a.hdr->sorted_buf ? a.pk[1] : a.pk[0];
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(256) k_bin_reduce_pay(BinArgs a) {
 // packed; otherwise the 8 B pixel boxes are gathered and converted.
 template <bool PACKED>
 __global__ void __launch_bounds__(256) k_bin_reduce(BinArgs a) {
+    pdl_enter();
     __shared__ unsigned long long ws[9];
     const uint32_t n = a.hdr->visible;
     const uint32_t *list = a.hdr->sorted_buf ? a.list[1] : a.list[0];
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(256) k_bin_reduce(BinArgs a) {
 }
 
 __global__ void __launch_bounds__(1024) k_bin_scan(BinArgs a) {
+    pdl_enter();
     __shared__ unsigned long long ws[33];
     constexpr int kPer = (kMaxSortCtas + 1023) / 1024;
     unsigned long long v[kPer], sum = 0;
@@ -179,6 +182,7 @@ __global__ void __launch_bounds__(1024) k_bin_scan(BinArgs a) {
 // payload or the count pass's packed copy); otherwise a.sbox.
 template <bool PACKED>
 __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
+    pdl_enter();
     constexpr int kRounds = kBinStep / 256;
     __shared__ uint32_t s_lp[kBinStep];       // large particles, per warp segment of 256, in list order
     __shared__ uint32_t s_loff[kBinStep];     // their first entry within the warp's run
@@ -315,6 +319,7 @@ __global__ void __launch_bounds__(256, 3) k_bin_emit(BinArgs a) {
 // bits): offsets[g] = first entry of group g, offsets[ngroups] = n.
 __global__ void __launch_bounds__(256) k_group_offsets(const uint32_t *count, const uint32_t *ids, uint32_t *off,
                                                        uint32_t ngroups) {
+    pdl_enter();
     const uint32_t n = *count;
     const uint32_t stride = gridDim.x * blockDim.x;
     if (n == 0) {
@@ -347,6 +352,7 @@ __device__ __forceinline__ FineRect key_rect(uint32_t key) {
 
 // Cut every super-tile's list into units of at most kUnit entries.
 __global__ void __launch_bounds__(1024) k_units(FineArgs a) {
+    pdl_enter();
     __shared__ uint32_t ws[33];
     uint32_t carry = 0;
     for (uint32_t base = 0; base < a.nsuper; base += 1024) {
@@ -377,6 +383,7 @@ __global__ void __launch_bounds__(1024) k_units(FineArgs a) {
 // fine tiles, accumulated as a 2-D difference array (four updates per entry)
 // and summed at the end.
 __global__ void __launch_bounds__(256) k_fine_count(FineArgs a) {
+    pdl_enter();
     __shared__ int diff[kSuperSide + 1][kSuperSide + 1];
     const uint32_t u = blockIdx.x;
     if (u >= a.hdr->n_units) return;
@@ -427,6 +434,7 @@ __global__ void __launch_bounds__(256) k_fine_count(FineArgs a) {
 // units are cut into 16 chunks: each chunk's sum, a scan over the chunks per
 // fine tile, then the running counts inside each chunk.
 __global__ void __launch_bounds__(1024) k_fine_unit_scan(FineArgs a) {
+    pdl_enter();
     constexpr int kChunks = 16;
     __shared__ uint32_t part[kChunks][64];
     const uint32_t s = blockIdx.x, t = threadIdx.x & 63u, g = threadIdx.x >> 6;
@@ -482,6 +490,7 @@ __global__ void __launch_bounds__(1024) k_fine_unit_scan(FineArgs a) {
 // Super-tile offsets from the digit totals of a single grouping pass (the
 // totals are the super-tiles' entry counts).
 __global__ void __launch_bounds__(256) k_soff_from_totals(const uint32_t *htot, uint32_t *off, uint32_t nsuper) {
+    pdl_enter();
     __shared__ uint32_t ws[9];
     const uint32_t t = threadIdx.x;
     uint32_t tot;
@@ -506,6 +515,7 @@ __device__ __forceinline__ int cost_class(uint32_t c) {
 // class is whatever the atomics give: the tiles are independent, so the
 // order changes when a tile runs, never the image.
 __global__ void __launch_bounds__(1024) k_fine_offsets(FineArgs a) {
+    pdl_enter();
     __shared__ unsigned long long ws[33];
     __shared__ uint32_t s_class[kCostClasses];
     constexpr int kPer = 8;
@@ -582,6 +592,7 @@ constexpr int kFineBuf = 6144;
 // the expansion waits on latency more than on issue (binning 0.573 -> 0.565
 // ms at 10M, 33.0 -> 32.6 ms at 1.07e9 against 46 registers and 5 CTAs)
 __global__ void __launch_bounds__(256, 7) k_fine_emit(FineArgs a) {
+    pdl_enter();
     __shared__ uint32_t s_buf[kFineBuf];
     __shared__ __align__(16) uint32_t s_b[8][16];   // per warp: row ballots 0..7, column ballots 8..15
     __shared__ uint32_t s_wcnt[8][64];              // per warp: its entries meeting each fine tile
@@ -770,12 +781,12 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     // the depth sort carried each particle's tile box (large frames), or the count pass
     // gathers the transform's packed tile boxes (the pixel boxes when the tile counts do
     // not fit 8 bits)
-    if (pay) k_bin_reduce_pay<<<a.ctas, 256, 0, st>>>(a);
-    else if (packed) k_bin_reduce<true><<<a.ctas, 256, 0, st>>>(a);
-    else k_bin_reduce<false><<<a.ctas, 256, 0, st>>>(a);
-    k_bin_scan<<<1, 1024, 0, st>>>(a);
-    if (packed) k_bin_emit<true><<<a.ctas, 256, 0, st>>>(a);
-    else k_bin_emit<false><<<a.ctas, 256, 0, st>>>(a);
+    if (pay) launch_pdl(k_bin_reduce_pay, dim3(a.ctas), dim3(256), 0, st, a);
+    else if (packed) launch_pdl(k_bin_reduce<true>, dim3(a.ctas), dim3(256), 0, st, a);
+    else launch_pdl(k_bin_reduce<false>, dim3(a.ctas), dim3(256), 0, st, a);
+    launch_pdl(k_bin_scan, dim3(1), dim3(1024), 0, st, a);
+    if (packed) launch_pdl(k_bin_emit<true>, dim3(a.ctas), dim3(256), 0, st, a);
+    else launch_pdl(k_bin_emit<false>, dim3(a.ctas), dim3(256), 0, st, a);
     count_launches(3);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -805,9 +816,9 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     const int f = passes & 1;
     const int sms = sm_count_bin();
     if (passes == 1)
-        k_soff_from_totals<<<1, 256, 0, st>>>(p.htot, at<uint32_t>(ws, L.off_soff), L.nsuper);
+        launch_pdl(k_soff_from_totals, dim3(1), dim3(256), 0, st, p.htot, at<uint32_t>(ws, L.off_soff), L.nsuper);
     else
-        k_group_offsets<<<sms * 8, 256, 0, st>>>(&hdr->super32, at<uint32_t>(ws, L.off_ek[f]),
+        launch_pdl(k_group_offsets, dim3(sms * 8), dim3(256), 0, st, &hdr->super32, at<uint32_t>(ws, L.off_ek[f]),
                                                  at<uint32_t>(ws, L.off_soff), L.nsuper);
     FineArgs fa{};
     fa.hdr = hdr;
@@ -827,11 +838,11 @@ cudaError_t launch_bin(void *ws, const Layout &L, uint32_t large_tiles, cudaStre
     fa.nty = (uint32_t)L.nty;
     fa.ntiles = L.ntiles;
     fa.max_units = L.max_units;
-    k_units<<<1, 1024, 0, st>>>(fa);
-    k_fine_count<<<L.max_units, 256, 0, st>>>(fa);
-    k_fine_unit_scan<<<L.nsuper, 1024, 0, st>>>(fa);
-    k_fine_offsets<<<1, 1024, 0, st>>>(fa);
-    k_fine_emit<<<L.max_units, 256, 0, st>>>(fa);
+    launch_pdl(k_units, dim3(1), dim3(1024), 0, st, fa);
+    launch_pdl(k_fine_count, dim3(L.max_units), dim3(256), 0, st, fa);
+    launch_pdl(k_fine_unit_scan, dim3(L.nsuper), dim3(1024), 0, st, fa);
+    launch_pdl(k_fine_offsets, dim3(1), dim3(1024), 0, st, fa);
+    launch_pdl(k_fine_emit, dim3(L.max_units), dim3(256), 0, st, fa);
     count_launches(6);
     return cudaGetLastError();
 }

@@ -140,4 +140,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
 // later asynchronous (bulk copy) writes to it.
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// --- programmatic dependent launch --------------------------------------------
+// A kernel launched with programmatic stream serialization (launch_pdl) may
+// be scheduled while the kernel before it on the stream finishes; it waits
+// here, before its first global memory access, until that kernel has
+// completed and its writes are visible, then lets the next kernel be
+// scheduled as its own CTAs drain.  Launched the ordinary way, both are
+// no-ops.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 }  // namespace spl

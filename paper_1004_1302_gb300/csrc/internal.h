@@ -19,6 +19,27 @@ constexpr int kSortTile = 4096;
 constexpr int kRadix = 256;
 constexpr int kMaxSortCtas = 2048;
 
+// Launch with programmatic stream serialization: the kernel's CTAs may be
+// scheduled while the previous kernel on the stream drains (every kernel of
+// the frame path starts with pdl_enter(), which waits for that kernel's
+// completion before touching memory), so the launch gap and the previous
+// kernel's last wave overlap.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Byte offsets of every workspace section.  Sections that depend only on the
 // particle count come first, so colorize can find its output from n alone.
 struct Layout {

@@ -664,6 +664,7 @@ __device__ __forceinline__ void render_any(const RenderArgs &a, const int tile, 
 // TMA: batches staged by tile::gather4 copies (tiles of 16 and 32, plain render).
 template <int T, int MODE, int B, bool ET, bool PT, bool TMA>
 __global__ void __launch_bounds__(render_threads(T), 1) k_render(RenderArgs a, const __grid_constant__ TmaMaps maps) {
+    pdl_enter();
     __shared__ __align__(16) RenderSmem<B> sm;
     const uint32_t tile = __ldg(&a.torder[blockIdx.x]);
     if (tile >= gridDim.x) return;   // a workspace that was never binned
@@ -713,9 +714,9 @@ __global__ void __launch_bounds__(render_threads(T)) k_render_batch(const __grid
 template <int T, int MODE, bool ET, bool PT, bool TMA>
 static void launch_tb(const RenderArgs &a, const TmaMaps &m, int ntiles, cudaStream_t st) {
     switch (a.batch) {
-    case 64: k_render<T, MODE, 64, ET, PT, TMA><<<ntiles, render_threads(T), 0, st>>>(a, m); break;
-    case 128: k_render<T, MODE, 128, ET, PT, TMA><<<ntiles, render_threads(T), 0, st>>>(a, m); break;
-    default: k_render<T, MODE, 256, ET, PT, TMA><<<ntiles, render_threads(T), 0, st>>>(a, m); break;
+    case 64: launch_pdl(k_render<T, MODE, 64, ET, PT, TMA>, dim3(ntiles), dim3(render_threads(T)), 0, st, a, m); break;
+    case 128: launch_pdl(k_render<T, MODE, 128, ET, PT, TMA>, dim3(ntiles), dim3(render_threads(T)), 0, st, a, m); break;
+    default: launch_pdl(k_render<T, MODE, 256, ET, PT, TMA>, dim3(ntiles), dim3(render_threads(T)), 0, st, a, m); break;
     }
 }
 

@@ -52,6 +52,7 @@ __device__ __forceinline__ uint32_t same_digit_lanes(uint32_t v) {
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(RadixPass P) {
+    pdl_enter();
     constexpr int kWarps = kSortThreads / 32;
     __shared__ uint32_t cnt[kWarps][kRadix];
     for (int q = threadIdx.x; q < kWarps * kRadix; q += blockDim.x) (&cnt[0][0])[q] = 0;
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(RadixPass P) {
 // One block per digit: exclusive scan of that digit's per-CTA counts and the
 // digit total.
 __global__ void __launch_bounds__(1024) k_radix_scan(RadixPass P) {
+    pdl_enter();
     __shared__ uint32_t warp_sums[33];
     if (pass_skipped(P)) return;
     const uint32_t d = blockIdx.x;
@@ -170,6 +172,7 @@ static_assert(sizeof(DsSmem<true>) + 1024 <= 228 * 1024 / kDsMinBlocksPay, "two 
 // the ballots are faster (10M: 0.295 against 0.356 ms).
 template <bool PAY>
 __global__ void __launch_bounds__(kDsThreads, PAY ? kDsMinBlocksPay : kDsMinBlocks) k_radix_downsweep(RadixPass P) {
+    pdl_enter();
     constexpr bool MATCH = PAY;
     extern __shared__ __align__(128) unsigned char ds_raw[];
     DsSmem<PAY> &sm = *reinterpret_cast<DsSmem<PAY> *>(ds_raw);
@@ -339,8 +342,7 @@ template <bool PAY> static cudaError_t launch_downsweep(const RadixPass &p, cuda
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit);
     }
-    k_radix_downsweep<PAY><<<p.ctas, kDsThreads, sizeof(DsSmem<PAY>), st>>>(p);
-    return cudaSuccess;
+    return launch_pdl(k_radix_downsweep<PAY>, dim3(p.ctas), dim3(kDsThreads), sizeof(DsSmem<PAY>), st, p);
 }
 
 cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st) {
@@ -348,8 +350,8 @@ cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st) {
     const uintptr_t al = reinterpret_cast<uintptr_t>(p.key_in) | reinterpret_cast<uintptr_t>(p.val_in) |
                          reinterpret_cast<uintptr_t>(p.pay_in);
     if (al & 15u) return cudaErrorInvalidValue;
-    k_radix_upsweep<<<p.ctas, kSortThreads, 0, st>>>(p);
-    k_radix_scan<<<kRadix, 1024, 0, st>>>(p);
+    launch_pdl(k_radix_upsweep, dim3(p.ctas), dim3(kSortThreads), 0, st, p);
+    launch_pdl(k_radix_scan, dim3(kRadix), dim3(1024), 0, st, p);
     const cudaError_t e = p.pay_out ? launch_downsweep<true>(p, st) : launch_downsweep<false>(p, st);
     if (e != cudaSuccess) return e;
     count_launches(3);
@@ -358,6 +360,7 @@ cudaError_t launch_radix_pass(const RadixPass &p, cudaStream_t st) {
 
 // Which ping-pong buffer holds the ordered visible list after the depth sort.
 __global__ void k_sort_finish(Header *hdr, int absorptive) {
+    pdl_enter();
     if (threadIdx.x != 0) return;
     uint32_t passes = 1;
     if (absorptive && hdr->visible) {
@@ -369,7 +372,7 @@ __global__ void k_sort_finish(Header *hdr, int absorptive) {
 }
 
 cudaError_t launch_sort_finish(Header *hdr, cudaStream_t st) {
-    k_sort_finish<<<1, 32, 0, st>>>(hdr, 1);
+    launch_pdl(k_sort_finish, dim3(1), dim3(32), 0, st, hdr, 1);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -425,7 +428,7 @@ cudaError_t launch_sort(void *ws, const Layout &L, int mode, cudaStream_t st) {
             if (e != cudaSuccess) return e;
         }
     }
-    k_sort_finish<<<1, 32, 0, st>>>(hdr, absorptive ? 1 : 0);
+    launch_pdl(k_sort_finish, dim3(1), dim3(32), 0, st, hdr, absorptive ? 1 : 0);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -8,6 +8,7 @@
 namespace spl {
 
 __global__ void k_init_header(Header *hdr, Layout L, int n_species, int mode, uint32_t boxes_kept) {
+    pdl_enter();
     if (threadIdx.x != 0) return;
     hdr->magic = kMagic;
     hdr->boxes_kept = boxes_kept;
@@ -97,6 +98,7 @@ __device__ __forceinline__ Footprint footprint(const TransformArgs &a, float x, 
 template <int kIlp>
 __global__ void __launch_bounds__(256) k_transform(TransformArgs a, float4 *geo, uint32_t *key, ushort4 *box,
                                                      Header *hdr) {
+    pdl_enter();
     uint32_t nvis = 0, kmin = kInvalidKey, kmax = 0;
     const uint64_t chunk = (uint64_t)kIlp * blockDim.x;
     for (uint64_t b = blockIdx.x * chunk; b < a.n; b += (uint64_t)gridDim.x * chunk) {
@@ -159,6 +161,7 @@ struct RangeJobs {
 };
 
 __global__ void __launch_bounds__(256) k_range(const __grid_constant__ RangeJobs jobs) {
+    pdl_enter();
     const RangeJob &J = jobs.job[blockIdx.y];
     const void *v = J.v;
     const int dtype = jobs.dtype, use_log = J.use_log;
@@ -193,6 +196,7 @@ __global__ void __launch_bounds__(256) k_range(const __grid_constant__ RangeJobs
 }
 
 __global__ void k_range_finish(Header *hdr, ColorizeArgs a) {
+    pdl_enter();
     const int s = threadIdx.x;
     const bool have = s < a.n_species;
     const bool empty = !have || a.begin[s + 1] == a.begin[s];
@@ -283,6 +287,7 @@ __device__ __forceinline__ float4 colorize_one(const ColorizeArgs &a, const Head
 // together and every store of a warp covers consecutive particles.
 template <int kIlp>
 __global__ void __launch_bounds__(256) k_colorize(ColorizeArgs a, const Header *hdr, float4 *col) {
+    pdl_enter();
     __shared__ float pal[SPLOTCH_MAX_PALETTE * 3];
     for (int k = threadIdx.x; k < a.n_entries * 3; k += blockDim.x) pal[k] = a.palette[k];
     __syncthreads();
@@ -321,7 +326,7 @@ static int sm_count() {
 }
 
 cudaError_t launch_init_header(void *ws, const Layout &L, int n_species, int mode, bool boxes_kept, cudaStream_t st) {
-    k_init_header<<<1, 32, 0, st>>>(header(ws), L, n_species, mode, boxes_kept ? 1u : 0u);
+    launch_pdl(k_init_header, dim3(1), dim3(32), 0, st, header(ws), L, n_species, mode, boxes_kept ? 1u : 0u);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -336,7 +341,7 @@ cudaError_t launch_transform(const TransformArgs &a, void *ws, const Layout &L, 
     constexpr int kIlp = 4;
     const uint64_t blocks = (a.n + kIlp * 256 - 1) / (kIlp * 256);
     const int grid = (int)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);
-    k_transform<kIlp><<<grid, 256, 0, st>>>(a, geo, key, box, header(ws));
+    launch_pdl(k_transform<kIlp>, dim3(grid), dim3(256), 0, st, a, geo, key, box, header(ws));
     count_launches(1);
     return cudaGetLastError();
 }
@@ -367,15 +372,15 @@ cudaError_t launch_colorize(const ColorizeArgs &a, void *ws, const Layout &L, cu
         const uint64_t want = (longest + 4 * 256 - 1) / (4 * 256);
         const uint64_t share = (uint64_t)sms * 8 / (uint64_t)nj;
         const unsigned gx = (unsigned)(want < share ? want : (share ? share : 1));
-        k_range<<<dim3(gx ? gx : 1, (unsigned)nj), 256, 0, st>>>(jobs);
+        launch_pdl(k_range, dim3(gx ? gx : 1, (unsigned)nj), dim3(256), 0, st, jobs);
         count_launches(1);
     }
-    k_range_finish<<<1, 32, 0, st>>>(header(ws), a);
+    launch_pdl(k_range_finish, dim3(1), dim3(32), 0, st, header(ws), a);
     count_launches(1);
     if (a.n) {
         uint64_t blocks = (a.n + 4 * 256 - 1) / (4 * 256);
         int grid = (int)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);
-        k_colorize<4><<<grid, 256, 0, st>>>(a, header(ws), at<float4>(ws, L.off_col));
+        launch_pdl(k_colorize<4>, dim3(grid), dim3(256), 0, st, a, header(ws), at<float4>(ws, L.off_col));
         count_launches(1);
     }
     return cudaGetLastError();
