@@ -160,6 +160,9 @@ struct RangeJobs {
     int dtype;
 };
 
+// loads in flight per thread in the range and colour passes (8 against 4:
+// transform + colour 0.1637 -> 0.1621 ms at 10M)
+constexpr int kRangeIlp = 8, kColorIlp = 8;
 __global__ void __launch_bounds__(256) k_range(const __grid_constant__ RangeJobs jobs) {
     pdl_enter();
     const RangeJob &J = jobs.job[blockIdx.y];
@@ -168,16 +171,16 @@ __global__ void __launch_bounds__(256) k_range(const __grid_constant__ RangeJobs
     const uint64_t begin = J.begin, end = J.end;
     float lo = INFINITY, hi = -INFINITY;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    // four independent loads in flight per thread
-    for (uint64_t i0 = begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < end; i0 += 4 * stride) {
-        float u[4];
+    // kRangeIlp independent loads in flight per thread
+    for (uint64_t i0 = begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < end; i0 += kRangeIlp * stride) {
+        float u[kRangeIlp];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kRangeIlp; ++k) {
             const uint64_t i = i0 + k * stride;
             u[k] = i < end ? load_value(v, dtype, i) : NAN;
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kRangeIlp; ++k) {
             if (i0 + k * stride >= end) continue;
             float w = u[k];
             // log10 is monotonic: the range of log10(max(v, 1e-37)) is taken from the
@@ -369,7 +372,7 @@ cudaError_t launch_colorize(const ColorizeArgs &a, void *ws, const Layout &L, cu
         jobs.dtype = a.dtype;
         // about eight CTAs per SM in all, shared by the jobs; none gets more CTAs than its
         // values fill
-        const uint64_t want = (longest + 4 * 256 - 1) / (4 * 256);
+        const uint64_t want = (longest + kRangeIlp * 256 - 1) / (kRangeIlp * 256);
         const uint64_t share = (uint64_t)sms * 8 / (uint64_t)nj;
         const unsigned gx = (unsigned)(want < share ? want : (share ? share : 1));
         launch_pdl(k_range, dim3(gx ? gx : 1, (unsigned)nj), dim3(256), 0, st, jobs);
@@ -378,9 +381,9 @@ cudaError_t launch_colorize(const ColorizeArgs &a, void *ws, const Layout &L, cu
     launch_pdl(k_range_finish, dim3(1), dim3(32), 0, st, header(ws), a);
     count_launches(1);
     if (a.n) {
-        uint64_t blocks = (a.n + 4 * 256 - 1) / (4 * 256);
+        uint64_t blocks = (a.n + kColorIlp * 256 - 1) / (kColorIlp * 256);
         int grid = (int)(blocks < (uint64_t)sms * 8 ? blocks : (uint64_t)sms * 8);
-        launch_pdl(k_colorize<4>, dim3(grid), dim3(256), 0, st, a, header(ws), at<float4>(ws, L.off_col));
+        launch_pdl(k_colorize<kColorIlp>, dim3(grid), dim3(256), 0, st, a, header(ws), at<float4>(ws, L.off_col));
         count_launches(1);
     }
     return cudaGetLastError();
