@@ -766,7 +766,7 @@ def figure_precision(args, dev, stream):
     return out
 
 
-def figure_north_star(args, dev, stream):
+def figure_full_lattice(args, dev, stream):
     """The whole 1024^3 (1.07e9-particle) lattice set, FP16 intensity, one
     1920x1080 absorptive frame."""
     import torch
@@ -1083,7 +1083,7 @@ def main():
             torch.cuda.empty_cache()
             out["precision"] = figure_precision(args, dev, stream)
             out["batching"] = figure_batching(args, dev, stream)
-            out["north_star"] = figure_north_star(args, dev, stream)
+            out["full_lattice_frame"] = figure_full_lattice(args, dev, stream)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
