@@ -86,6 +86,7 @@ struct Header {
     uint32_t range_lo_enc[SPLOTCH_MAX_SPECIES];   // order-preserving encodings for atomic min/max
     uint32_t range_hi_enc[SPLOTCH_MAX_SPECIES];
     float lo[SPLOTCH_MAX_SPECIES], hi[SPLOTCH_MAX_SPECIES];
+    float inv_span[SPLOTCH_MAX_SPECIES];     // 1 / (hi - lo) (0 when hi <= lo)
     uint32_t vlo_enc[SPLOTCH_MAX_SPECIES][3], vhi_enc[SPLOTCH_MAX_SPECIES][3];   // vector components
     uint32_t qlo_enc[SPLOTCH_MAX_SPECIES], qhi_enc[SPLOTCH_MAX_SPECIES];         // modulating scalar
     float vlo[SPLOTCH_MAX_SPECIES][3], vhi[SPLOTCH_MAX_SPECIES][3], qmax[SPLOTCH_MAX_SPECIES];

@@ -86,7 +86,10 @@ __device__ __forceinline__ Footprint footprint(const TransformArgs &a, float x, 
     float y0 = ly > 0.0f ? ly : 0.0f, y1 = hy < a.h_max ? hy : a.h_max;
     if (!(lx <= hx) || !(ly <= hy) || !(x0 <= x1) || !(y0 <= y1)) return f;
     f.key = __float_as_uint(Zf);
-    f.geo = make_float4(px, py, __fmul_rn(r, r), __fdiv_rn(-1.4426950408889634f, __fmul_rn(sg, sg)));
+    // k = -log2(e) / sigma_pix^2 feeds only the weight's exponent (the oracle
+    // evaluates the weight in FP64 from sigma_pix), so the fast division's
+    // 2 ulp are enough
+    f.geo = make_float4(px, py, __fmul_rn(r, r), __fdividef(-1.4426950408889634f, __fmul_rn(sg, sg)));
     f.box = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
     return f;
 }
@@ -237,6 +240,7 @@ __global__ void k_range_finish(Header *hdr, ColorizeArgs a) {
     if (isnan(hi)) hi = empty ? 0.0f : (lg ? log10f(ordered_to_float(hdr->range_hi_enc[s])) : ordered_to_float(hdr->range_hi_enc[s]));
     hdr->lo[s] = lo;
     hdr->hi[s] = hi;
+    hdr->inv_span[s] = hi > lo ? 1.0f / (hi - lo) : 0.0f;
     if (a.sp[s].use_vector && !empty)
         for (int c = 0; c < 3; ++c) {
             hdr->vlo[s][c] = ordered_to_float(hdr->vlo_enc[s][c]);
@@ -264,7 +268,7 @@ __device__ __forceinline__ float4 colorize_one(const ColorizeArgs &a, const Head
     } else if (sp.use_colormap) {
         if (sp.use_log) u = log10f(fmaxf(u, 1e-37f));
         const float lo = hdr->lo[s], hi = hdr->hi[s];
-        float t = hi > lo ? __fdiv_rn(u - lo, hi - lo) : 0.0f;
+        float t = hi > lo ? (u - lo) * hdr->inv_span[s] : 0.0f;   // 1 / (hi - lo), once per species
         t = fminf(fmaxf(t, 0.0f), 1.0f);
         float w = t * kmax;
         int k = min((int)floorf(w), a.n_entries - 2);
