@@ -25,6 +25,12 @@
  * found on the device (for example a tile-entry capacity overflow) are
  * written to a status word inside the workspace and reported by
  * splotch_frame_info.  No call aborts, traps or throws.
+ *
+ * The kernels of a frame are launched with programmatic stream
+ * serialization (programmatic dependent launch): a kernel may be scheduled
+ * while the one before it on the stream drains, but waits for it to complete
+ * before it touches memory, so stream order holds for the caller's own work
+ * before and after these calls.
  */
 #ifndef SPLOTCH_H
 #define SPLOTCH_H
