@@ -166,33 +166,87 @@ struct RangeJobs {
 // loads in flight per thread in the range and colour passes (8 against 4:
 // transform + colour 0.1637 -> 0.1621 ms at 10M)
 constexpr int kRangeIlp = 8, kColorIlp = 8;
+// The values of one 16-byte vector as floats: 4 (FP32) or 8 (FP16, BF16).
+template <int DT> struct Vec16;
+template <> struct Vec16<0> {
+    static constexpr int kN = 4;
+    __device__ static void unpack(const uint4 q, float *o) {
+        o[0] = __uint_as_float(q.x); o[1] = __uint_as_float(q.y); o[2] = __uint_as_float(q.z); o[3] = __uint_as_float(q.w);
+    }
+};
+template <> struct Vec16<1> {
+    static constexpr int kN = 8;
+    __device__ static void unpack(const uint4 q, float *o) {
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            o[2 * k] = __half2float(__ushort_as_half((unsigned short)(w[k] & 0xFFFFu)));
+            o[2 * k + 1] = __half2float(__ushort_as_half((unsigned short)(w[k] >> 16)));
+        }
+    }
+};
+template <> struct Vec16<2> {
+    static constexpr int kN = 8;
+    __device__ static void unpack(const uint4 q, float *o) {
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {   // bfloat16: the upper half of a float
+            o[2 * k] = __uint_as_float(w[k] << 16);
+            o[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+        }
+    }
+};
+
+// Extremes of one job's values: 16-byte vector loads over the aligned body
+// (kRangeIlp in flight per thread), single loads for the unaligned ends.
+template <int DT>
+__device__ __forceinline__ void range_extremes(const RangeJob &J, int use_log, float &lo, float &hi) {
+    constexpr int kN = Vec16<DT>::kN;
+    auto take = [&](float w) {
+        // log10 is monotonic: the range of log10(max(v, 1e-37)) is taken from the
+        // extremes of max(v, 1e-37), and the logarithm applied to those two only
+        if (use_log) w = fmaxf(w, 1e-37f);
+        lo = fminf(lo, w);
+        hi = fmaxf(hi, w);
+    };
+    const uint64_t begin = J.begin, end = J.end;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, nthr = (uint64_t)gridDim.x * blockDim.x;
+    const bool aligned = (reinterpret_cast<uintptr_t>(J.v) & 15u) == 0;
+    const uint64_t vb = aligned ? (begin + kN - 1) / kN : end, ve = aligned ? end / kN : end;   // whole vectors
+    if (!aligned || vb >= ve) {
+        for (uint64_t i = begin + tid; i < end; i += nthr) take(load_value(J.v, DT, i));
+        return;
+    }
+    // the ends: elements before the first and after the last whole vector
+    const uint64_t head = vb * kN - begin, tail = end - ve * kN;
+    if (tid < head) take(load_value(J.v, DT, begin + tid));
+    else if (tid < head + tail) take(load_value(J.v, DT, ve * kN + (tid - head)));
+    const uint4 *q = reinterpret_cast<const uint4 *>(J.v);
+    for (uint64_t v0 = vb + tid; v0 < ve; v0 += kRangeIlp * nthr) {
+        uint4 r[kRangeIlp];
+#pragma unroll
+        for (int k = 0; k < kRangeIlp; ++k) {
+            const uint64_t vi = v0 + k * nthr;
+            if (vi < ve) r[k] = q[vi];
+        }
+#pragma unroll
+        for (int k = 0; k < kRangeIlp; ++k) {
+            if (v0 + k * nthr >= ve) continue;
+            float o[kN];
+            Vec16<DT>::unpack(r[k], o);
+#pragma unroll
+            for (int e = 0; e < kN; ++e) take(o[e]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_range(const __grid_constant__ RangeJobs jobs) {
     pdl_enter();
     const RangeJob &J = jobs.job[blockIdx.y];
-    const void *v = J.v;
-    const int dtype = jobs.dtype, use_log = J.use_log;
-    const uint64_t begin = J.begin, end = J.end;
     float lo = INFINITY, hi = -INFINITY;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    // kRangeIlp independent loads in flight per thread
-    for (uint64_t i0 = begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < end; i0 += kRangeIlp * stride) {
-        float u[kRangeIlp];
-#pragma unroll
-        for (int k = 0; k < kRangeIlp; ++k) {
-            const uint64_t i = i0 + k * stride;
-            u[k] = i < end ? load_value(v, dtype, i) : NAN;
-        }
-#pragma unroll
-        for (int k = 0; k < kRangeIlp; ++k) {
-            if (i0 + k * stride >= end) continue;
-            float w = u[k];
-            // log10 is monotonic: the range of log10(max(v, 1e-37)) is taken from the
-            // extremes of max(v, 1e-37), and the logarithm applied to those two only
-            if (use_log) w = fmaxf(w, 1e-37f);
-            lo = fminf(lo, w);
-            hi = fmaxf(hi, w);
-        }
-    }
+    if (jobs.dtype == 1) range_extremes<1>(J, J.use_log, lo, hi);
+    else if (jobs.dtype == 2) range_extremes<2>(J, J.use_log, lo, hi);
+    else range_extremes<0>(J, J.use_log, lo, hi);
     uint32_t elo = __reduce_min_sync(0xFFFFFFFFu, float_to_ordered(lo));
     uint32_t ehi = __reduce_max_sync(0xFFFFFFFFu, float_to_ordered(hi));
     if (lane_id() == 0) {
